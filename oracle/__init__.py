@@ -1,0 +1,253 @@
+"""Oracle for the all-sky string ISW map -- TEST INFRASTRUCTURE ONLY.
+
+A ctypes wrapper around ``isw_oracle.c``: a plain single-threaded FP64 C restatement of
+the paper's method (Eq. 1-2, Sec. II.A-D) that shares no code with the CUDA library.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package.  Threads here only split independent pixels (or samples)
+across calls of the single-threaded C routines; ctypes releases the GIL during a call.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "isw_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle_isw.so")
+_lib = None
+_lock = threading.Lock()
+
+OK, EINVAL, EDOMAIN, ENOCONV = 0, 1, 3, 4
+LINEAR, BURDEN = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE evaluation order: -ffp-contract=off)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-Wall",
+               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.or_sincospi_frac.argtypes = [ctypes.c_int64, ctypes.c_int64, _dp, _dp]
+            L.or_sincospi_frac.restype = None
+            L.or_sincos_turns.argtypes = [ctypes.c_double, _dp, _dp]
+            L.or_sincos_turns.restype = None
+            L.or_pix2vec_ring.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _i64p,
+                                          _dp, ctypes.c_int64, _i64p, _i64p]
+            L.or_pix2vec_ring.restype = ctypes.c_int
+            L.or_burden_eval.argtypes = [_dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                         ctypes.c_double, _dp]
+            L.or_burden_eval.restype = None
+            L.or_lightcone.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, ctypes.c_int64, _dp,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _dp,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp,
+                                       _i32p]
+            L.or_lightcone.restype = ctypes.c_int
+            L.or_pair_term.argtypes = [_dp, _dp, _dp, ctypes.c_double]
+            L.or_pair_term.restype = ctypes.c_double
+            L.or_isw_map.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _i64p, _dp,
+                                     ctypes.c_int64, ctypes.c_int64, _dp, ctypes.c_double, _dp,
+                                     _i64p]
+            L.or_isw_map.restype = ctypes.c_int
+            L.or_isw_sum_dirs.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, _dp, ctypes.c_int64,
+                                          ctypes.c_int64, _dp, ctypes.c_double, _dp]
+            L.or_isw_sum_dirs.restype = ctypes.c_int
+            L.or_isw_map_adjoint.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _i64p,
+                                             _dp, ctypes.c_int64, ctypes.c_int64, _dp,
+                                             ctypes.c_double, _dp, _dp, ctypes.c_int64, ctypes.c_int]
+            L.or_isw_map_adjoint.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def sincospi_frac(a: int, b: int):
+    """(sin, cos) of pi*a/b with exact integer angle reduction."""
+    s, c = ctypes.c_double(), ctypes.c_double()
+    lib().or_sincospi_frac(int(a), int(b), ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def sincos_turns(w: float):
+    """(sin, cos) of 2*pi*w, reduction in turns."""
+    s, c = ctypes.c_double(), ctypes.c_double()
+    lib().or_sincos_turns(float(w), ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def pix2vec_ring(nside: int, pix=None, pix0: int = 0, n: int | None = None):
+    """RING pixel centres: returns (vec [3, n], ring [n], j [n]) (ring 1..4N-1, j 1-based)."""
+    if pix is not None:
+        pix = np.ascontiguousarray(pix, dtype=np.int64)
+        n = pix.size
+    elif n is None:
+        n = 12 * nside * nside - pix0
+    vec = np.empty((3, n))
+    ring = np.empty(n, dtype=np.int64)
+    jj = np.empty(n, dtype=np.int64)
+    st = lib().or_pix2vec_ring(nside, pix0, n, pix.ctypes.data_as(_i64p) if pix is not None else None,
+                               _d(vec), n, ring.ctypes.data_as(_i64p), jj.ctypes.data_as(_i64p))
+    if st:
+        raise ValueError(f"or_pix2vec_ring failed with status {st}")
+    return vec, ring, jj
+
+
+def burden_eval(loop_params, loop_id: int, sigma: float, t: float):
+    """(X, Xdot, X') of Burden loop ``loop_id`` at (sigma, t)."""
+    P = _c64(loop_params)
+    out = np.empty(9)
+    lib().or_burden_eval(_d(P), P.shape[1], loop_id, sigma, t, _d(out))
+    return out[0:3], out[3:6], out[6:9]
+
+
+def default_tol(t_obs: float = 1.0) -> float:
+    """Light-cone residual tolerance: 4 ulp of t_obs."""
+    return 4.0 * float(np.nextafter(t_obs, np.inf) - t_obs)
+
+
+def lightcone(mode: int, nodes, loop_params=None, t_box: float = 0.0, x_obs=(0.0, 0.0, 0.0),
+              t_obs: float = 1.0, tol: float | None = None, max_iter: int = 60):
+    """Samples on the past light cone: returns (samples [10, n], tau [n], status [n])."""
+    nodes = _c64(nodes)
+    n = nodes.shape[1]
+    P = _c64(loop_params if loop_params is not None else np.zeros((17, 0)))
+    xo = _c64(x_obs)
+    out = np.empty_like(nodes)
+    tau = np.empty(n)
+    status = np.empty(n, dtype=np.int32)
+    lib().or_lightcone(int(mode), _d(nodes), n, n, _d(P) if P.size else None, P.shape[1],
+                       max(P.shape[1], 1), float(t_box), _d(xo), float(t_obs),
+                       default_tol(t_obs) if tol is None else float(tol), int(max_iter),
+                       _d(out), _d(tau), status.ctypes.data_as(_i32p))
+    return out, tau, status
+
+
+def lightcone_workload(w):
+    """Light-cone samples of every shell of a ``synth.Workload`` (concatenated)."""
+    parts, taus, sts = [], [], []
+    for k in range(w.nshell):
+        nodes, t_box, mode = w.shell(k)
+        s, tau, st = lightcone(mode, nodes, w.loop_params, t_box, w.x_obs, w.t_obs)
+        parts.append(s)
+        taus.append(tau)
+        sts.append(st)
+    return np.concatenate(parts, axis=1), np.concatenate(taus), np.concatenate(sts)
+
+
+def pair_term(nvec, sample10, x_obs=(0.0, 0.0, 0.0), GU: float = 1.0) -> float:
+    """One term of the discrete Eq. (1) for direction nvec and one 10-double sample."""
+    return lib().or_pair_term(_d(_c64(nvec)), _d(_c64(sample10)), _d(_c64(x_obs)), float(GU))
+
+
+def _split(n, parts):
+    parts = max(1, min(parts, n))
+    b = np.linspace(0, n, parts + 1).astype(np.int64)
+    return [(int(b[i]), int(b[i + 1])) for i in range(parts) if b[i + 1] > b[i]]
+
+
+def isw_map(nside: int, samples, pix=None, x_obs=(0.0, 0.0, 0.0), GU: float = 1.0,
+            threads: int = 1):
+    """Theta at RING pixels ``pix`` (all pixels when None); returns (theta, stats[2])."""
+    samples = _c64(samples)
+    n = samples.shape[1]
+    if pix is None:
+        pix = np.arange(12 * nside * nside, dtype=np.int64)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    theta = np.empty(pix.size)
+    xo = _c64(x_obs)
+    L = lib()
+    stats_all = []
+    errors = []
+
+    def work(a, b):
+        st = np.zeros(2, dtype=np.int64)
+        sub = np.ascontiguousarray(pix[a:b])
+        out = np.empty(b - a)
+        r = L.or_isw_map(nside, 0, b - a, sub.ctypes.data_as(_i64p), _d(samples), n, n, _d(xo),
+                         float(GU), _d(out), st.ctypes.data_as(_i64p))
+        if r:
+            errors.append(r)
+        theta[a:b] = out
+        stats_all.append(st)
+
+    ranges = _split(pix.size, threads)
+    ths = [threading.Thread(target=work, args=r) for r in ranges]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    if errors:
+        raise ValueError(f"or_isw_map failed with status {errors[0]}")
+    stats = np.array([sum(s[0] for s in stats_all), stats_all[0][1] if stats_all else 0])
+    return theta, stats
+
+
+def isw_sum_dirs(dirs, samples, x_obs=(0.0, 0.0, 0.0), GU: float = 1.0):
+    """The discrete Eq. (1) at explicit unit directions ``dirs`` [3, k] (off the HEALPix grid)."""
+    dirs = _c64(dirs)
+    samples = _c64(samples)
+    out = np.empty(dirs.shape[1])
+    r = lib().or_isw_sum_dirs(dirs.shape[1], _d(dirs), dirs.shape[1], _d(samples), samples.shape[1],
+                              samples.shape[1], _d(_c64(x_obs)), float(GU), _d(out))
+    if r:
+        raise ValueError(f"or_isw_sum_dirs failed with status {r}")
+    return out
+
+
+def isw_map_adjoint(nside: int, samples, g_pix, pix=None, x_obs=(0.0, 0.0, 0.0), GU: float = 1.0,
+                    ngrad: int = 6, threads: int = 1):
+    """dL/d(X, Xdot[, X']) per sample for a per-pixel dL/dTheta: returns grad [ngrad, n]."""
+    samples = _c64(samples)
+    n = samples.shape[1]
+    if pix is None:
+        pix = np.arange(12 * nside * nside, dtype=np.int64)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    g_pix = _c64(g_pix)
+    assert g_pix.size == pix.size
+    grad = np.zeros((ngrad, n))
+    xo = _c64(x_obs)
+    L = lib()
+    errors = []
+
+    def work(a, b):
+        sub = np.ascontiguousarray(samples[:, a:b])
+        out = np.empty((ngrad, b - a))
+        r = L.or_isw_map_adjoint(nside, 0, pix.size, pix.ctypes.data_as(_i64p), _d(sub), b - a,
+                                 b - a, _d(xo), float(GU), _d(g_pix), _d(out), b - a, int(ngrad))
+        if r:
+            errors.append(r)
+        grad[:, a:b] = out
+
+    ranges = _split(n, threads)
+    ths = [threading.Thread(target=work, args=r) for r in ranges]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    if errors:
+        raise ValueError(f"or_isw_map_adjoint failed with status {errors[0]}")
+    return grad

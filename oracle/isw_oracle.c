@@ -1,0 +1,605 @@
+/*
+ * Oracle for the all-sky string ISW map -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded FP64 restatement of what the GPU library computes,
+ * written from the paper (Ringeval & Bouchet, "All sky CMB map from cosmic strings
+ * integrated Sachs-Wolfe effect", arXiv:1204.5041) and from the published HEALPix
+ * geometry (Gorski et al. 2005).  Only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it; the product path never does.  It shares no code,
+ * header or constant with the CUDA library.
+ *
+ * Built with -O2 -ffp-contract=off: every expression below is evaluated as written,
+ * with IEEE double rounding of each operation and no fused multiply-add.
+ *
+ * Contents
+ *   1. sincos of an angle given as an exact fraction of a turn (own series, no libm trig)
+ *   2. HEALPix RING pix2vec (Sec. II.D; Gorski et al. 2005 ring geometry)
+ *   3. retarded-time (past light cone) solve, LINEAR and BURDEN modes (Eq. 1: X cap x_gamma)
+ *   4. per-segment weight eps*dsigma (text after Eq. 1) and the pair term of Eq. (1)-(2)
+ *   5. the discrete line-of-sight sum per pixel, Neumaier-compensated, input order
+ *   6. the analytic adjoint of the sum with respect to X and Xdot (and optionally X')
+ *
+ * Pins (tests/test_oracle_*.py) tie each part to something other than itself; see the
+ * header comment of each section for what pins it.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <stdlib.h>
+
+/* pi rounded to the nearest double */
+static const double PI = 3.14159265358979323846264338327950288;
+
+#define OR_OK 0
+#define OR_EINVAL 1
+#define OR_EDOMAIN 3
+#define OR_ENOCONV 4
+
+/* ------------------------------------------------------------------------------------
+ * 1. sin/cos on [0, pi/4] by the Taylor series, and exact octant reduction.
+ *
+ * For x = f*pi/4 with f in [0, 1]: x2 = x*x, term_0 = x (sin) or 1 (cos), each next
+ * term = (previous * x2) / (2k(2k+1)) for sin and / ((2k-1)2k) for cos, k = 1..10, and
+ * the alternating series is summed from the smallest term (k = 10) down to k = 0.
+ * The angle is reduced exactly: to octant k and a fraction f of it, folding odd octants
+ * so the series always sees x in [0, pi/4].  Pinned against mpmath (test_oracle_sincos).
+ * ---------------------------------------------------------------------------------- */
+#define NTERMS 10
+
+static void sincos_octant(double f, double *s, double *c)
+{
+    const double quarter_pi = PI * 0.25;
+    double x = f * quarter_pi;
+    double x2 = x * x;
+    double st[NTERMS + 1], ct[NTERMS + 1];
+    st[0] = x;
+    ct[0] = 1.0;
+    for (int k = 1; k <= NTERMS; ++k) {
+        st[k] = (st[k - 1] * x2) / (double)((2 * k) * (2 * k + 1));
+        ct[k] = (ct[k - 1] * x2) / (double)((2 * k - 1) * (2 * k));
+    }
+    double S = 0.0, C = 0.0;
+    for (int k = NTERMS; k >= 0; --k) {
+        if (k & 1) {
+            S = S - st[k];
+            C = C - ct[k];
+        } else {
+            S = S + st[k];
+            C = C + ct[k];
+        }
+    }
+    *s = S;
+    *c = C;
+}
+
+/* Map (sin, cos) of the folded octant angle back to the full angle (k*pi/4 + ...). */
+static void octant_unfold(int k, double sf, double cf, double *s, double *c)
+{
+    switch (k & 7) {
+    case 0: *s = sf;  *c = cf;  break;
+    case 1: *s = cf;  *c = sf;  break;
+    case 2: *s = cf;  *c = -sf; break;
+    case 3: *s = sf;  *c = -cf; break;
+    case 4: *s = -sf; *c = -cf; break;
+    case 5: *s = -cf; *c = -sf; break;
+    case 6: *s = -cf; *c = sf;  break;
+    default: *s = -sf; *c = cf; break;
+    }
+}
+
+/* sin and cos of pi*a/b for integers a, b > 0 (exact integer reduction). */
+void or_sincospi_frac(int64_t a, int64_t b, double *s, double *c)
+{
+    int64_t m = 8 * b;
+    int64_t A = (4 * a) % m;
+    if (A < 0) A += m;
+    int64_t k = A / b;
+    int64_t r = A - k * b;
+    double f = (k & 1) ? (double)(b - r) / (double)b : (double)r / (double)b;
+    double sf, cf;
+    sincos_octant(f, &sf, &cf);
+    octant_unfold((int)k, sf, cf, s, c);
+}
+
+/* sin and cos of 2*pi*w for a double w (reduction in turns: exact for |w| < 2^52). */
+void or_sincos_turns(double w, double *s, double *c)
+{
+    double wr = w - floor(w);
+    if (wr >= 1.0) wr = 0.0;
+    double e = wr * 8.0;
+    double kd = floor(e);
+    double r = e - kd;
+    int k = (int)kd;
+    double f = (k & 1) ? 1.0 - r : r;
+    double sf, cf;
+    sincos_octant(f, &sf, &cf);
+    octant_unfold(k, sf, cf, s, c);
+}
+
+/* ------------------------------------------------------------------------------------
+ * 2. HEALPix RING pixel centres (Sec. II.D of the paper; geometry of Gorski et al. 2005).
+ *
+ * Rings are numbered 1..4N-1 from the north pole.  North polar cap: ring i < N holds 4i
+ * pixels, z = 1 - i^2/(3N^2), phi = pi (2j-1)/(4i).  Equatorial belt N <= i <= 3N: 4N
+ * pixels, z = 4/3 - 2i/(3N), phi = pi (2j - s)/(4N) with s = 2 when i + N is odd and
+ * s = 1 when it is even (rings alternate between a pixel centred on phi = 0 and a half-pixel
+ * offset; the first pixel of a ring is the one at or just after phi = 0).  South cap
+ * mirrors the north.  z and sin(theta) are formed from exact integers with one division:
+ *   caps:    z = +-(3N^2 - i^2) / (3N^2),  sin(theta) = i * sqrt(6N^2 - i^2) / (3N^2)
+ *   belt:    z = (4N - 2i) / (3N),         sin(theta) = sqrt((2i - N)(7N - 2i)) / (3N)
+ * Pinned by brute-force ring enumeration, exact rational z, the equal-area identity and
+ * reflection / rotation symmetries (test_oracle_pix2vec).
+ * ---------------------------------------------------------------------------------- */
+static int64_t isqrt64(int64_t v)
+{
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r > 0 && r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+int or_pix2vec_ring_one(int64_t nside, int64_t p, int64_t *ring, int64_t *jpix, double vec[3])
+{
+    const int64_t N = nside;
+    const int64_t npix = 12 * N * N;
+    const int64_t ncap = 2 * N * (N - 1);
+    if (N < 1 || p < 0 || p >= npix) return OR_EINVAL;
+    int64_t i, j, a, b;
+    double z, st;
+    if (p < ncap) {
+        i = (1 + isqrt64(1 + 2 * p)) / 2;
+        j = p - 2 * i * (i - 1) + 1;
+        z = (double)(3 * N * N - i * i) / (double)(3 * N * N);
+        st = ((double)i * sqrt((double)(6 * N * N - i * i))) / (double)(3 * N * N);
+        a = 2 * j - 1;
+        b = 4 * i;
+        *ring = i;
+    } else if (p < npix - ncap) {
+        int64_t q = p - ncap;
+        i = q / (4 * N) + N;
+        j = q % (4 * N) + 1;
+        int64_t s = ((i + N) & 1) ? 2 : 1;
+        z = (double)(4 * N - 2 * i) / (double)(3 * N);
+        st = sqrt((double)((2 * i - N) * (7 * N - 2 * i))) / (double)(3 * N);
+        a = 2 * j - s;
+        b = 4 * N;
+        *ring = i;
+    } else {
+        int64_t q = npix - p;
+        i = (1 + isqrt64(2 * q - 1)) / 2;
+        j = 4 * i + 1 - (q - 2 * i * (i - 1));
+        z = -((double)(3 * N * N - i * i) / (double)(3 * N * N));
+        st = ((double)i * sqrt((double)(6 * N * N - i * i))) / (double)(3 * N * N);
+        a = 2 * j - 1;
+        b = 4 * i;
+        *ring = 4 * N - i;
+    }
+    *jpix = j;
+    double sp, cp;
+    or_sincospi_frac(a, b, &sp, &cp);
+    vec[0] = st * cp;
+    vec[1] = st * sp;
+    vec[2] = z;
+    return OR_OK;
+}
+
+/* n pixels, ring indices in pix (or pix0 + k when pix == NULL); out double[3][ld]. */
+int or_pix2vec_ring(int64_t nside, int64_t pix0, int64_t n, const int64_t *pix,
+                    double *vec, int64_t ld, int64_t *ring, int64_t *jpix)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t p = pix ? pix[k] : pix0 + k;
+        int64_t ri, ji;
+        double v[3];
+        int st = or_pix2vec_ring_one(nside, p, &ri, &ji, v);
+        if (st) return st;
+        vec[k] = v[0];
+        vec[ld + k] = v[1];
+        vec[2 * ld + k] = v[2];
+        if (ring) ring[k] = ri;
+        if (jpix) jpix[k] = ji;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------
+ * 3. Past-light-cone solve: the integral of Eq. (1) runs over the string points X that
+ * intercept the photon path x_gamma, i.e. |X(tau) - x_obs| = t_obs - tau (flat conformal
+ * coordinates, c = 1).  The paper records X', Xdot at the crossing (Sec. II.B).
+ *
+ * LINEAR: straight worldline X + Xdot*Delta from box time t_box.  With r0 = X - x_obs,
+ * T = t_obs - t_box: (v^2 - 1) D^2 + 2 (r0.Xdot + T) D + (|r0|^2 - T^2) = 0; the past root
+ * is D = -c / (b + sqrt(b^2 + (1 - v^2) c)) with b = r0.Xdot + T, c = (|r0| - T)(|r0| + T).
+ * Xdot, X', dsigma are carried unchanged.  Pinned by closed forms (static node; radial
+ * motion) and the light-cone residual (test_oracle_lightcone).
+ *
+ * BURDEN: analytic loop X(s,t) = c + R (a(s - (t - t0)) + b(s + (t - t0)))/2 with
+ * a(u) = L/(2 pi m) (sin 2 pi m u/L, -cos 2 pi m u/L, 0) and
+ * b(v) = L/(2 pi n) (sin 2 pi n v/L, -cos(psi) cos 2 pi n v/L, -sin(psi) cos 2 pi n v/L).
+ * f(t) = |X(s,t) - x_obs| - (t_obs - t) is increasing; safeguarded Newton on the bracket
+ * [t_obs - d - L/2, t_obs - d + L/2] (d = |c - x_obs|), stop when |f| <= tol.
+ * ---------------------------------------------------------------------------------- */
+static void burden_eval(const double *P, int64_t ldp, int64_t id, double sigma, double t,
+                        double X[3], double Xd[3], double Xp[3])
+{
+    const double two_pi = 2.0 * PI;
+    double c[3], R[9];
+    for (int k = 0; k < 3; ++k) c[k] = P[k * ldp + id];
+    for (int k = 0; k < 9; ++k) R[k] = P[(3 + k) * ldp + id];
+    double L = P[12 * ldp + id], m = P[13 * ldp + id], n = P[14 * ldp + id];
+    double psi = P[15 * ldp + id], t0 = P[16 * ldp + id];
+    double dt = t - t0;
+    double u = sigma - dt, v = sigma + dt;
+    double sa, ca, sb, cb, sp, cp;
+    or_sincos_turns((m * u) / L, &sa, &ca);
+    or_sincos_turns((n * v) / L, &sb, &cb);
+    or_sincos_turns(psi / two_pi, &sp, &cp);
+    double ra = L / (two_pi * m), rb = L / (two_pi * n);
+    double a[3] = {ra * sa, -(ra * ca), 0.0};
+    double b[3] = {rb * sb, -(rb * (cp * cb)), -(rb * (sp * cb))};
+    double ap[3] = {ca, sa, 0.0};
+    double bp[3] = {cb, cp * sb, sp * sb};
+    double h[3], hd[3], hp[3];
+    for (int k = 0; k < 3; ++k) {
+        h[k] = 0.5 * (a[k] + b[k]);
+        hd[k] = 0.5 * (bp[k] - ap[k]);
+        hp[k] = 0.5 * (ap[k] + bp[k]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        X[k] = c[k] + ((R[3 * k] * h[0] + R[3 * k + 1] * h[1]) + R[3 * k + 2] * h[2]);
+        Xd[k] = (R[3 * k] * hd[0] + R[3 * k + 1] * hd[1]) + R[3 * k + 2] * hd[2];
+        Xp[k] = (R[3 * k] * hp[0] + R[3 * k + 1] * hp[1]) + R[3 * k + 2] * hp[2];
+    }
+}
+
+/* Burden worldsheet at (sigma, t) for loop id (exposed for tests). */
+void or_burden_eval(const double *P, int64_t ldp, int64_t id, double sigma, double t,
+                    double *out9)
+{
+    burden_eval(P, ldp, id, sigma, t, out9, out9 + 3, out9 + 6);
+}
+
+int or_lightcone(int mode, const double *nodes, int64_t n, int64_t ld,
+                 const double *P, int64_t nloops, int64_t ldp, double t_box,
+                 const double x_obs[3], double t_obs, double tol, int max_iter,
+                 double *out, double *tau, int32_t *status)
+{
+    int worst = OR_OK;
+    for (int64_t s = 0; s < n; ++s) {
+        int st = OR_OK;
+        double X[3], Xd[3], Xp[3], t = t_obs;
+        if (mode == 0) {
+            double r0[3];
+            for (int k = 0; k < 3; ++k) {
+                X[k] = nodes[k * ld + s];
+                Xd[k] = nodes[(3 + k) * ld + s];
+                Xp[k] = nodes[(6 + k) * ld + s];
+                r0[k] = X[k] - x_obs[k];
+            }
+            double R = sqrt((r0[0] * r0[0] + r0[1] * r0[1]) + r0[2] * r0[2]);
+            double T = t_obs - t_box;
+            double v2 = (Xd[0] * Xd[0] + Xd[1] * Xd[1]) + Xd[2] * Xd[2];
+            double om = 1.0 - v2;
+            if (!(om > 0.0) || !(R == R)) {
+                st = OR_EDOMAIN;
+                t = t_box;
+            } else {
+                double c = (R - T) * (R + T);
+                double bh = ((r0[0] * Xd[0] + r0[1] * Xd[1]) + r0[2] * Xd[2]) + T;
+                double disc = bh * bh + om * c;
+                if (disc < 0.0) disc = 0.0;
+                double D = -c / (bh + sqrt(disc));
+                t = t_box + D;
+                for (int k = 0; k < 3; ++k) X[k] = X[k] + Xd[k] * D;
+            }
+        } else {
+            int64_t id = (int64_t)nodes[s];
+            double sigma = nodes[ld + s];
+            if (id < 0 || id >= nloops) {
+                st = OR_EINVAL;
+                for (int k = 0; k < 3; ++k) X[k] = Xd[k] = Xp[k] = 0.0;
+            } else {
+                double cx = P[0 * ldp + id] - x_obs[0];
+                double cy = P[1 * ldp + id] - x_obs[1];
+                double cz = P[2 * ldp + id] - x_obs[2];
+                double d = sqrt((cx * cx + cy * cy) + cz * cz);
+                double halfL = 0.5 * P[12 * ldp + id];
+                double lo = (t_obs - d) - halfL, hi = (t_obs - d) + halfL;
+                t = t_obs - d;
+                st = OR_ENOCONV;
+                for (int it = 0; it < max_iter; ++it) {
+                    burden_eval(P, ldp, id, sigma, t, X, Xd, Xp);
+                    double r[3] = {X[0] - x_obs[0], X[1] - x_obs[1], X[2] - x_obs[2]};
+                    double rn = sqrt((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]);
+                    double f = rn - (t_obs - t);
+                    if (fabs(f) <= tol) {
+                        st = OR_OK;
+                        break;
+                    }
+                    if (!(rn > 0.0)) {
+                        st = OR_EDOMAIN;
+                        break;
+                    }
+                    if (f < 0.0) lo = t; else hi = t;
+                    double fp = 1.0 + ((r[0] * Xd[0] + r[1] * Xd[1]) + r[2] * Xd[2]) / rn;
+                    double tn = t - f / fp;
+                    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+                    if (it + 1 < max_iter) t = tn;
+                }
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            out[k * ld + s] = X[k];
+            out[(3 + k) * ld + s] = Xd[k];
+            out[(6 + k) * ld + s] = Xp[k];
+        }
+        out[9 * ld + s] = nodes[9 * ld + s];
+        if (tau) tau[s] = t;
+        if (status) status[s] = st;
+        if (st > worst) worst = st;
+    }
+    return worst;
+}
+
+/* ------------------------------------------------------------------------------------
+ * 4. The pair term of Eq. (1)-(2).
+ *
+ *   Theta(n) = -4 GU sum_s u.D / D^2 * eps_s dsigma_s,  D = X n - X_s,  X = |X_s - x_obs|,
+ *   u = Xdot - (n.X') X' / (1 + n.Xdot),  eps^2 = X'^2 / (1 - Xdot^2).
+ *
+ * D is formed as X * (n - Xhat) with the unit vector Xhat = (X_s - x_obs)/X carried in
+ * double-double (hi + lo): near a string n - Xhat cancels, and an FP64-rounded Xhat would
+ * leave D with a relative error of ~1e-16 / |n - Xhat|.  D = 0 exactly gives a zero term
+ * (counted); a segment with 1 - Xdot^2 <= 0 or a non-finite weight contributes nothing
+ * (counted).  Pinned by an independent mpmath evaluation of Eq. (1)-(2), the Kaiser-
+ * Stebbins step of a straight moving string and brute-force quadrature (tests).
+ * ---------------------------------------------------------------------------------- */
+
+/* Error-free transformations (Knuth two-sum, Dekker split product: no FMA needed). */
+static void two_sum(double a, double b, double *s, double *e)
+{
+    double x = a + b;
+    double bb = x - a;
+    *e = (a - (x - bb)) + (b - bb);
+    *s = x;
+}
+
+static void split(double a, double *hi, double *lo)
+{
+    const double factor = 134217729.0; /* 2^27 + 1 */
+    double t = factor * a;
+    *hi = t - (t - a);
+    *lo = a - *hi;
+}
+
+static void two_prod(double a, double b, double *p, double *e)
+{
+    double ah, al, bh, bl;
+    double x = a * b;
+    split(a, &ah, &al);
+    split(b, &bh, &bl);
+    *e = ((ah * bh - x) + ah * bl + al * bh) + al * bl;
+    *p = x;
+}
+
+/* Unit vector r/|r| with each component as hi + lo (relative accuracy ~1e-30). */
+static void unit_dd(const double r[3], double hi[3], double lo[3], double *norm)
+{
+    /* |r|^2 in double-double */
+    double sh = 0.0, sl = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double p, pe, s, se;
+        two_prod(r[k], r[k], &p, &pe);
+        two_sum(sh, p, &s, &se);
+        sl = sl + (se + pe);
+        two_sum(s, sl, &sh, &sl);
+    }
+    /* |r| = sqrt in double-double: one Newton correction of the double root */
+    double q = sqrt(sh);
+    double qq, qqe;
+    two_prod(q, q, &qq, &qqe);
+    double ql = (((sh - qq) - qqe) + sl) / (2.0 * q);
+    double nh, nl;
+    two_sum(q, ql, &nh, &nl);
+    *norm = nh;
+    /* r_k / (nh + nl) in double-double: quotient, remainder, correction */
+    for (int k = 0; k < 3; ++k) {
+        double q1 = r[k] / nh;
+        double p, pe;
+        two_prod(q1, nh, &p, &pe);
+        double rem = ((r[k] - p) - pe) - q1 * nl;
+        double q2 = rem / nh;
+        two_sum(q1, q2, &hi[k], &lo[k]);
+    }
+}
+
+typedef struct {
+    double xh[3], xl[3]; /* Xhat as double-double */
+    double X;            /* |X_s - x_obs| */
+    double xd[3], xp[3]; /* Xdot, X' */
+    double kappa;        /* -4 GU eps dsigma */
+    double om;           /* 1 - Xdot^2 */
+    double xp2;          /* X'^2 */
+    int ok;
+} seg_t;
+
+static void seg_prepare(const double *samples, int64_t ld, int64_t s, const double x_obs[3],
+                        double GU, seg_t *g)
+{
+    double r[3];
+    for (int k = 0; k < 3; ++k) {
+        r[k] = samples[k * ld + s] - x_obs[k];
+        g->xd[k] = samples[(3 + k) * ld + s];
+        g->xp[k] = samples[(6 + k) * ld + s];
+    }
+    double dsig = samples[9 * ld + s];
+    unit_dd(r, g->xh, g->xl, &g->X);
+    double v2 = (g->xd[0] * g->xd[0] + g->xd[1] * g->xd[1]) + g->xd[2] * g->xd[2];
+    g->om = 1.0 - v2;
+    g->xp2 = (g->xp[0] * g->xp[0] + g->xp[1] * g->xp[1]) + g->xp[2] * g->xp[2];
+    double eps = sqrt(g->xp2 / g->om);
+    g->kappa = -4.0 * GU * (eps * dsig);
+    g->ok = (g->om > 0.0) && (g->X > 0.0) && isfinite(g->kappa);
+}
+
+/* u.D / D^2 pieces for one (pixel, segment) pair; returns 0 when D = 0 exactly. */
+typedef struct {
+    double D[3], D2, A, B, u[3], uD, XpD;
+} pair_t;
+
+static int pair_eval(const double n[3], const seg_t *g, pair_t *q)
+{
+    for (int k = 0; k < 3; ++k) q->D[k] = g->X * ((n[k] - g->xh[k]) - g->xl[k]);
+    q->D2 = (q->D[0] * q->D[0] + q->D[1] * q->D[1]) + q->D[2] * q->D[2];
+    if (q->D2 == 0.0) return 0;
+    q->A = (n[0] * g->xp[0] + n[1] * g->xp[1]) + n[2] * g->xp[2];
+    q->B = 1.0 + ((n[0] * g->xd[0] + n[1] * g->xd[1]) + n[2] * g->xd[2]);
+    for (int k = 0; k < 3; ++k) q->u[k] = g->xd[k] - (q->A * g->xp[k]) / q->B;
+    q->uD = (q->u[0] * q->D[0] + q->u[1] * q->D[1]) + q->u[2] * q->D[2];
+    q->XpD = (g->xp[0] * q->D[0] + g->xp[1] * q->D[1]) + g->xp[2] * q->D[2];
+    return 1;
+}
+
+/* One pair term (for pins): n[3], one sample (10 doubles, row stride 1). */
+double or_pair_term(const double n[3], const double sample10[10], const double x_obs[3],
+                    double GU)
+{
+    seg_t g;
+    pair_t q;
+    seg_prepare(sample10, 1, 0, x_obs, GU, &g);
+    if (!g.ok) return 0.0;
+    if (!pair_eval(n, &g, &q)) return 0.0;
+    return g.kappa * (q.uD / q.D2);
+}
+
+/* ------------------------------------------------------------------------------------
+ * 5. The map: for every requested pixel, the sum over all samples in input order with
+ * Neumaier compensation (the discrete form of Eq. (1), Sec. III.A: no segment is cut).
+ * Pixels are RING indices pix[k] (or pix0 + k).  stats (optional, int64[2]): number of
+ * D = 0 pairs, number of samples skipped for 1 - Xdot^2 <= 0.
+ * ---------------------------------------------------------------------------------- */
+int or_isw_map(int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix,
+               const double *samples, int64_t n, int64_t ld, const double x_obs[3], double GU,
+               double *theta, int64_t *stats)
+{
+    int64_t zero_pairs = 0, bad = 0;
+    seg_t *segs = (seg_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(seg_t));
+    if (!segs) return OR_EINVAL;
+    for (int64_t s = 0; s < n; ++s) {
+        seg_prepare(samples, ld, s, x_obs, GU, &segs[s]);
+        if (!segs[s].ok) ++bad;
+    }
+    for (int64_t k = 0; k < npix; ++k) {
+        int64_t p = pix ? pix[k] : pix0 + k, ri, ji;
+        double nv[3];
+        int st = or_pix2vec_ring_one(nside, p, &ri, &ji, nv);
+        if (st) {
+            free(segs);
+            return st;
+        }
+        double sum = 0.0, comp = 0.0;
+        for (int64_t s = 0; s < n; ++s) {
+            pair_t q;
+            if (!segs[s].ok) continue;
+            if (!pair_eval(nv, &segs[s], &q)) {
+                ++zero_pairs;
+                continue;
+            }
+            double t = segs[s].kappa * (q.uD / q.D2);
+            double x = sum + t;
+            if (fabs(sum) >= fabs(t)) comp += (sum - x) + t;
+            else comp += (t - x) + sum;
+            sum = x;
+        }
+        theta[k] = sum + comp;
+    }
+    free(segs);
+    if (stats) {
+        stats[0] = zero_pairs;
+        stats[1] = bad;
+    }
+    return OR_OK;
+}
+
+/* Same sum for explicit unit directions dirs[3][ld_dir] (for pins off the HEALPix grid). */
+int or_isw_sum_dirs(int64_t ndir, const double *dirs, int64_t ld_dir, const double *samples,
+                    int64_t n, int64_t ld, const double x_obs[3], double GU, double *theta)
+{
+    seg_t *segs = (seg_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(seg_t));
+    if (!segs) return OR_EINVAL;
+    for (int64_t s = 0; s < n; ++s) seg_prepare(samples, ld, s, x_obs, GU, &segs[s]);
+    for (int64_t k = 0; k < ndir; ++k) {
+        double nv[3] = {dirs[k], dirs[ld_dir + k], dirs[2 * ld_dir + k]};
+        double sum = 0.0, comp = 0.0;
+        for (int64_t s = 0; s < n; ++s) {
+            pair_t q;
+            if (!segs[s].ok || !pair_eval(nv, &segs[s], &q)) continue;
+            double t = segs[s].kappa * (q.uD / q.D2);
+            double x = sum + t;
+            if (fabs(sum) >= fabs(t)) comp += (sum - x) + t;
+            else comp += (t - x) + sum;
+            sum = x;
+        }
+        theta[k] = sum + comp;
+    }
+    free(segs);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------
+ * 6. Adjoint.  With t = kappa (u.D)/D^2, kappa = -4 GU eps dsigma:
+ *   dt/dX_s    = kappa [ (h.n) Xhat - h ],  h = u/D^2 - 2 (u.D) D / D^4   (dD/dX_s = n Xhat^T - I)
+ *   dt/dXdot   = t Xdot/(1 - Xdot^2) + kappa [ D + A (X'.D) n / B^2 ] / D^2
+ *   dt/dX'     = t X'/X'^2 - kappa [ (X'.D) n + A D ] / (B D^2)
+ * and dL/dq_s = sum_p g_p dt_ps/dq_s.  grad is double[ngrad][ldg] with rows X(3), Xdot(3)
+ * and, when ngrad == 9, X'(3).  Pinned by central finite differences of the oracle map.
+ * ---------------------------------------------------------------------------------- */
+int or_isw_map_adjoint(int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix,
+                       const double *samples, int64_t n, int64_t ld, const double x_obs[3],
+                       double GU, const double *g_pix, double *grad, int64_t ldg, int ngrad)
+{
+    double *nvs = (double *)malloc((size_t)(npix > 0 ? npix : 1) * 3 * sizeof(double));
+    if (!nvs) return OR_EINVAL;
+    for (int64_t k = 0; k < npix; ++k) {
+        int64_t p = pix ? pix[k] : pix0 + k, ri, ji;
+        int st = or_pix2vec_ring_one(nside, p, &ri, &ji, nvs + 3 * k);
+        if (st) {
+            free(nvs);
+            return st;
+        }
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        seg_t g;
+        seg_prepare(samples, ld, s, x_obs, GU, &g);
+        double acc[9] = {0}, cmp[9] = {0};
+        for (int64_t k = 0; k < npix && g.ok; ++k) {
+            const double *nv = nvs + 3 * k;
+            pair_t q;
+            if (!pair_eval(nv, &g, &q)) continue;
+            double gp = g_pix[k];
+            double t = g.kappa * (q.uD / q.D2);
+            double inv = 1.0 / q.D2;
+            double h[3];
+            for (int c = 0; c < 3; ++c) h[c] = q.u[c] * inv - 2.0 * q.uD * q.D[c] * inv * inv;
+            double hn = (h[0] * nv[0] + h[1] * nv[1]) + h[2] * nv[2];
+            double xhat[3] = {g.xh[0] + g.xl[0], g.xh[1] + g.xl[1], g.xh[2] + g.xl[2]};
+            double d[9];
+            double B2 = q.B * q.B;
+            for (int c = 0; c < 3; ++c) {
+                d[c] = g.kappa * (hn * xhat[c] - h[c]);
+                d[3 + c] = t * g.xd[c] / g.om + g.kappa * (q.D[c] + q.A * q.XpD * nv[c] / B2) * inv;
+                d[6 + c] = t * g.xp[c] / g.xp2 - g.kappa * (q.XpD * nv[c] + q.A * q.D[c]) / (q.B * q.D2);
+            }
+            for (int c = 0; c < ngrad; ++c) {
+                double tt = gp * d[c];
+                double x = acc[c] + tt;
+                if (fabs(acc[c]) >= fabs(tt)) cmp[c] += (acc[c] - x) + tt;
+                else cmp[c] += (tt - x) + acc[c];
+                acc[c] = x;
+            }
+        }
+        for (int c = 0; c < ngrad; ++c) grad[c * ldg + s] = acc[c] + cmp[c];
+    }
+    free(nvs);
+    return OR_OK;
+}
