@@ -1,0 +1,338 @@
+"""Benchmark: pixel-segment pairs per second of the full-sky string ISW map.
+
+Workload (default): Nside=512 RING sky (3,145,728 pixels) and one box of 200,000 light-cone
+samples -- 234 Burden loops x 512 nodes (BURDEN light-cone solve) plus 8 random-walk long
+strings of 10,024 nodes at box time 0.6 (LINEAR solve) -- seeded synthetic inputs.
+
+One step = the whole hot path on that input: light-cone solve of every node, pixel table
+(RING pix2vec), sample records, the all-pairs map in the FP32-compensated precision (FP64
+near field), written as a float64 RING map.  Inputs are resident in HBM before the timed
+region; L2 (129 MB) is flushed between steps by writing a 256 MiB buffer outside the timed
+events.  `e2e` repeats the step through the public Python API with the nodes copied from
+pinned host memory and the map copied back every step.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pixel-segment pairs/s (FP32-compensated map; FP64 GPU path and %FP32 peak reported)"
+UNIT = "pairs/s"
+FLOPS_PER_PAIR = 36          # algorithmic flops of one Eq. (1)-(2) pair term, FMA = 2
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops():
+    """Dense FP32 peak from unit counts and the maximum SM clock: SMs x 128 lanes x 2 flop x clock."""
+    mhz = _peaks().get("sm_max_mhz", 2070.0)
+    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def workload_config(w):
+    return {
+        "workload": f"{w.name}: Nside={w.nside} RING ({w.npix:,} pixels), {w.n:,} light-cone samples "
+                    f"(234 Burden loops x 512 + 8 random-walk strings), {w.nshell} shells",
+        "nside": w.nside, "npix": w.npix, "samples": w.n, "pairs_per_step": w.npix * w.n,
+        "precision": "FP32 pairs, compensated per-pixel sums, FP64 near field",
+        "l2": "flushed between steps (256 MiB write outside the timed events)",
+        "inputs": "seeded synthetic string network (synth.config(1)) standing in for the paper's simulations",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1204_5041_gb300 as isw
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    # weak scaling: every rank maps its own independent string network (seed + rank)
+    w = synth.config(1, seed=args.seed + rank)
+    ctx = isw.default_context(local)
+    nodes_h = torch.from_numpy(np.ascontiguousarray(w.nodes)).pin_memory()
+    loops_h = torch.from_numpy(np.ascontiguousarray(w.loop_params)).pin_memory()
+    loops_d = loops_h.to(dev)
+    nodes_d = nodes_h.to(dev)
+    samples_d = torch.empty_like(nodes_d)
+    theta_d = torch.empty(w.npix, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(nodes, samples, theta, prec="f32c"):
+        for k in range(w.nshell):
+            a, b = int(w.shell_off[k]), int(w.shell_off[k + 1])
+            isw.lightcone_intersect(int(w.mode[k]), nodes[:, a:b], loops_d, float(w.t_box[k]), w.x_obs, w.t_obs,
+                                    out=samples[:, a:b])
+        isw.isw_map(w.nside, samples, x_obs=w.x_obs, GU=w.GU, prec=prec, out=theta)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(nodes_d, samples_d, theta_d)
+    r, counts = ctx.check_status()
+    if r != isw.OK:
+        raise RuntimeError(f"device status {r} during warm-up: {ctx.last_error()}")
+
+    # ---- timed region: K steps, per-step events, L2 flushed between steps (not timed)
+    ctx.set_param(isw.PARAM_TIMING, 1)
+    ctx.timing(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record(stream)
+            step(nodes_d, samples_d, theta_d)
+            e1.record(stream)
+        barrier()
+    t_wall = time.perf_counter() - t_wall
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    map_ms, map_launches, all_launches = ctx.timing(reset=True)
+    ctx.set_param(isw.PARAM_TIMING, 0)
+    r, counts = ctx.check_status()
+    if r != isw.OK:
+        raise RuntimeError(f"device status {r} in the timed region: {ctx.last_error()}")
+    total_ms = float(sum(ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pairs_step = w.npix * w.n
+    value = ws * pairs_step * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API: pinned host nodes in, map out, every step
+    theta_h = torch.empty(w.npix, dtype=torch.float64).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        nd = nodes_h.to(dev, non_blocking=True)
+        loops_d.copy_(loops_h, non_blocking=True)
+        step(nd, samples_d, theta_d)
+        theta_h.copy_(theta_d, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = ws * pairs_step / (e2e_ms / 1e3)
+
+    # ---- plain FP64 GPU path, one step (outside the timed region), for the FP32/FP64 ratio
+    fp64 = None
+    if not args.skip_fp64:
+        theta64 = torch.empty_like(theta_d)
+        barrier()
+        e0.record(stream)
+        step(nodes_d, samples_d, theta64, prec="f64")
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": pairs_step / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64}
+
+    peak, mhz = fp32_peak_tflops()
+    map_avg_ms = map_ms / max(map_launches, 1)
+    achieved = FLOPS_PER_PAIR * pairs_step / (map_avg_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "isw::k_map_f32c<256,4,64>", "flops_per_pair": FLOPS_PER_PAIR,
+            "kernel_ms": map_avg_ms,
+            "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz (max SM clock)"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload_config(w),
+        "clocks": clk.summary(), "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int((nodes_h.numel() + loops_h.numel()) * 8),
+                "d2h_bytes_per_step": int(theta_h.numel() * 8), "ms_per_step": e2e_ms},
+        "gpu_launches": int(all_launches),
+        "fp64": fp64, "speedup_fp32c_vs_fp64": (value / ws) / fp64["value"] if fp64 else None,
+        "counts_per_step": {k: v / args.steps for k, v in counts.items()},
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and not args.skip_cpu:
+        out["cpu_baseline"] = cpu_baseline(w, theta_d, theta64 if fp64 else None, args)
+    if ws > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def _oracle_sample(w, samples, npix_sample, seed=0):
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(w.npix, npix_sample, replace=False)).astype(np.int64)
+    threads = os.cpu_count() or 1
+    t = time.perf_counter()
+    ref, _ = oracle.isw_map(w.nside, samples, pix=pix, x_obs=w.x_obs, GU=w.GU, threads=threads)
+    dt = time.perf_counter() - t
+    return pix, ref, dt, threads
+
+
+def cpu_baseline(w, theta32_d, theta64_d, args):
+    """The oracle as it stands, on this host's cores, on a bounded pixel sample of the same
+    workload (all samples, light-cone solved by the oracle), sized to ~15 s; also the GPU
+    maps' error on those pixels."""
+    import oracle
+
+    samples, _, _ = oracle.lightcone_workload(w)
+    probe = 64
+    _, _, dt, _ = _oracle_sample(w, samples, probe, seed=1)
+    npix_sample = int(min(w.npix, max(probe, probe * args.cpu_seconds / max(dt, 1e-3))))
+    pix, ref, dt, threads = _oracle_sample(w, samples, npix_sample)
+    rms = float(np.sqrt(np.mean(ref ** 2)))
+    res = {"value": npix_sample * w.n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{npix_sample} random pixels x all {w.n} samples ({npix_sample * w.n:.3e} pairs, {dt:.1f} s)"}
+    g32 = theta32_d.cpu().numpy()[pix]
+    res["max_err_fp32c_rel_rms"] = float(np.max(np.abs(g32 - ref)) / rms)
+    res["rms_err_fp32c_rel_rms"] = float(np.sqrt(np.mean((g32 - ref) ** 2)) / rms)
+    if theta64_d is not None:
+        g64 = theta64_d.cpu().numpy()[pix]
+        res["max_err_fp64_rel_rms"] = float(np.max(np.abs(g64 - ref)) / rms)
+    res["map_rms"] = rms
+    return res
+
+
+def run_reference(args):
+    """Reference arm: the oracle (plain single-threaded C per thread) on the host cores."""
+    import oracle
+
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = synth.config(1, seed=args.seed)
+    samples, _, st = oracle.lightcone_workload(w)
+    threads = os.cpu_count() or 1
+    probe = 32
+    _, _, dt, _ = _oracle_sample(w, samples, probe, seed=1)
+    per_step = int(max(probe, probe * args.ref_step_seconds / max(dt, 1e-3)))
+    for k in range(args.warmup):
+        _oracle_sample(w, samples, max(probe, per_step // 8), seed=100 + k)
+    t = time.perf_counter()
+    tot_pairs = 0
+    for k in range(args.steps):
+        s, _, _ = oracle.lightcone_workload(w)  # the light-cone solve is part of the step
+        _oracle_sample(w, s, per_step, seed=200 + k)
+        tot_pairs += per_step * w.n
+    dt = time.perf_counter() - t
+    value = tot_pairs / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"each step: light-cone solve of all nodes + {per_step} random pixels x "
+                                      f"all {w.n} samples"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=6.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * isw.h -- C ABI of the GB300 (sm_103a) full-sky string ISW map library (libisw.so).
+ *
+ * The library evaluates the all-sky integrated Sachs-Wolfe temperature shift sourced by
+ * Nambu-Goto strings on the observer's past light cone, Eq. (1)-(2) of Ringeval & Bouchet,
+ * "All sky CMB map from cosmic strings integrated Sachs-Wolfe effect" (arXiv:1204.5041):
+ *
+ *   Theta(n) = -4 GU  sum_s  u.D / D^2  eps_s dsigma_s,    D = X n - X_s,  X = |X_s - x_obs|,
+ *   u = Xdot - (n.X') X' / (1 + n.Xdot),                 eps^2 = X'^2 / (1 - Xdot^2),
+ *
+ * for every HEALPix RING pixel direction n (Sec. II.D), summed over every string sample s
+ * on the light cone (Sec. II.A, Sec. III.A: no segment is cut).
+ *
+ * Units and conventions: flat conformal coordinates, c = 1; the observer sits at x_obs at
+ * conformal time t_obs (horizon units: x_obs = 0, t_obs = 1).  GU is the string tension in
+ * Planck units; maps scale linearly with it.
+ *
+ * Memory: every array argument is a DEVICE pointer owned by the caller (for example a
+ * PyTorch CUDA tensor's data pointer), except where marked (host).  Arrays of several rows
+ * are row-major "double[rows][ld]": element (r, k) sits at base[r * ld + k].  The library
+ * allocates only its own workspace, held in the context and freed by isw_destroy.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).  Every compute
+ * call only enqueues work on it and returns; results are ready when the stream is.
+ *
+ * Errors: every call returns an isw_status.  Argument errors (ISW_EINVAL) are found on the
+ * host before anything is enqueued.  Conditions found on the device (a sample with
+ * |Xdot| >= 1, a light-cone iteration that did not converge, a bounded wait that ran out)
+ * are recorded in a device status word and returned by isw_check_status, which
+ * synchronises the stream.  The message of the last error is available from
+ * isw_last_error.  No C++ exception crosses this interface.
+ *
+ * Threads: a context may be used by one host thread at a time; use one context per
+ * thread (they may share a device).
+ */
+#ifndef ISW_H
+#define ISW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct isw_ctx isw_ctx;
+
+typedef enum {
+    ISW_OK = 0,
+    ISW_EINVAL = 1,   /* bad argument: null pointer, host pointer where a device one is due, bad size */
+    ISW_ECUDA = 2,    /* a CUDA runtime call failed (message in isw_last_error) */
+    ISW_EDOMAIN = 3,  /* a sample with 1 - Xdot^2 <= 0 or a non-finite weight (skipped) */
+    ISW_ENOCONV = 4,  /* a light-cone solve hit its iteration cap */
+    ISW_ETIMEOUT = 5, /* a bounded device-side wait ran out (the kernel returned early) */
+    ISW_ENOMEM = 6    /* workspace allocation failed */
+} isw_status;
+
+/* precision of the pair arithmetic */
+enum { ISW_F64 = 0, ISW_F32C = 1 };
+/* light-cone solve mode */
+enum { ISW_LINEAR = 0, ISW_BURDEN = 1 };
+/* isw_map_batched flags */
+enum { ISW_SKIP_LIGHTCONE = 1, ISW_GRAPH = 2, ISW_AUTOTUNE = 4 };
+/* isw_set_param keys */
+enum { ISW_PARAM_NEAR_K = 0, ISW_PARAM_B_MIN = 1, ISW_PARAM_SPLIT = 2, ISW_PARAM_VARIANT = 3, ISW_PARAM_TIMING = 4 };
+
+/* Create a context bound to CUDA device `device`.  Allocates a small device status block.
+ * Returns ISW_EINVAL for a bad device index, ISW_ECUDA / ISW_ENOMEM on CUDA failures. */
+int isw_create(isw_ctx **ctx, int device);
+
+/* Free the context and its workspace (synchronises the device first). */
+int isw_destroy(isw_ctx *ctx);
+
+/* Message of the last error on this context ("" when none).  Owned by the context. */
+const char *isw_last_error(const isw_ctx *ctx);
+
+/* Synchronise `stream`, then return and clear the device status: ISW_ETIMEOUT, ISW_ENOCONV
+ * or ISW_EDOMAIN (in that order of precedence) if any kernel recorded one since the last
+ * call, else ISW_OK.  counts (host, may be NULL) receives 3 counters accumulated since the
+ * last call: pairs with D = 0 exactly (zero term), skipped samples (|Xdot| >= 1 or
+ * non-finite weight), pairs that the FP32 path evaluated in FP64 (near field). */
+int isw_check_status(isw_ctx *ctx, void *stream, int64_t *counts);
+
+/* Tunables: ISW_PARAM_NEAR_K (default 4): a pair is "near" when the chord |n - Xhat| is
+ * below near_k * max(pixel size, angular length of the sample's segment); ISW_PARAM_B_MIN
+ * (default 0.01): a pair with 1 + n.Xdot below b_min is evaluated in FP64 by the FP32 path;
+ * ISW_PARAM_SPLIT: number of segment chunks of the forward maps (0 = automatic);
+ * ISW_PARAM_VARIANT: FP32 kernel variant (-1 = automatic); ISW_PARAM_TIMING (default 0):
+ * when 1, every launch of the pair kernel (the all-pairs sum of isw_map and
+ * isw_map_batched) is bracketed by CUDA events on its stream, read by isw_get_timing. */
+int isw_set_param(isw_ctx *ctx, int key, double value);
+
+/* Timing of the pair kernel (ISW_PARAM_TIMING = 1): synchronises the recorded events and
+ * returns in *ms the summed device time of the pair-kernel launches recorded since the last
+ * reset, in *pair_launches their number and in *all_launches the number of kernels of any
+ * kind this context launched in that interval (counted whether or not timing is on).  All
+ * three are host pointers and may be NULL.  reset = 1 clears the record.  At most 4096
+ * pair-kernel launches are timed between resets (later ones are counted, not timed). */
+int isw_get_timing(isw_ctx *ctx, double *ms, int64_t *pair_launches, int64_t *all_launches, int reset);
+
+/* Pixel centres, HEALPix RING scheme (Sec. II.D; Gorski et al. 2005 geometry).
+ *   nside    : resolution N >= 1 (N_pix = 12 N^2), N <= 2^24
+ *   pix_list : device int64[npix] of RING indices, or NULL for the range pix0 .. pix0+npix-1
+ *   vec_out  : device double[3][ld_out] receiving (x, y, z) of each pixel, ld_out >= npix
+ * The directions are bit-identical to the published specification of this library: exact
+ * integer ring arithmetic, IEEE-rounded z and sin(theta), and an own sin/cos series.
+ * Indices outside [0, N_pix) write NaN and set ISW_EINVAL in the device status. */
+int hp_pix2vec_ring(isw_ctx *ctx, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list,
+                    double *vec_out, int64_t ld_out, void *stream);
+
+/* Past-light-cone intersection (Eq. 1: the string points X with X cap x_gamma; Sec. II.B:
+ * X' and Xdot are recorded at the crossing).
+ *   mode = ISW_LINEAR: nodes_in is double[10][ld]: X(3), Xdot(3), X'(3), dsigma at box time
+ *          t_box; the worldline X + Xdot*D meets |X - x_obs| = t_obs - tau at the past root
+ *          D = tau - t_box (closed form); Xdot, X', dsigma are carried unchanged.
+ *   mode = ISW_BURDEN: nodes_in rows 0, 1 are (loop id, sigma) and row 9 dsigma; loop_params
+ *          is double[17][ldp] per loop: centre (3), rotation (9, row-major), L, m, n, psi,
+ *          t0; the sample is the analytic Burden worldsheet at the retarded time, found by
+ *          safeguarded Newton iteration (at most 60 steps, residual <= 4 ulp of t_obs).
+ *   x_obs    : host double[3]; t_obs: observer time (> t_box for LINEAR)
+ *   samples_out : device double[10][ld_out] (X, Xdot, X', dsigma on the cone)
+ *   tau_out  : device double[n] retarded times (may be NULL)
+ *   status   : device int32[n] per-node status (ISW_OK, ISW_EDOMAIN, ISW_ENOCONV, ISW_EINVAL),
+ *              may be NULL; any non-OK node is also recorded in the context status.
+ * The arithmetic is IEEE double without contraction, reproducible operation by operation. */
+int lightcone_intersect(isw_ctx *ctx, int mode, const double *nodes_in, int64_t n, int64_t ld,
+                        const double *loop_params, int64_t nloops, int64_t ldp, double t_box,
+                        const double *x_obs, double t_obs, double *samples_out, int64_t ld_out,
+                        double *tau_out, int32_t *status, void *stream);
+
+/* The map of Eq. (1)-(2) (Sec. III.A: every pixel sums every sample, none cut).
+ *   nside, pix0, npix, pix_list : pixels as in hp_pix2vec_ring; npix = 12 N^2 with
+ *              pix0 = 0 and pix_list = NULL selects the full sky (processed in compact tiles)
+ *   samples  : device double[10][ld] on the light cone (output of lightcone_intersect)
+ *   x_obs    : host double[3] (NULL = origin); GU: tension
+ *   prec     : ISW_F32C (FP32 pair arithmetic with per-pixel compensated sums; near-field
+ *              pairs and pairs with 1 + n.Xdot < b_min in FP64) or ISW_F64 (all FP64)
+ *   accumulate : 0 writes theta_out, 1 adds to it
+ *   theta_out: device double[npix] in the order of the selected pixels
+ * A pair with D = 0 contributes zero; a sample with |Xdot| >= 1 contributes nothing (both
+ * counted in the device status).  The result is deterministic (fixed reduction order). */
+int isw_map(isw_ctx *ctx, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list,
+            const double *samples, int64_t n, int64_t ld, const double *x_obs, double GU, int prec,
+            int accumulate, double *theta_out, void *stream);
+
+/* Adjoint of isw_map with respect to the samples (an extension of the method: the
+ * derivative of Eq. (1)-(2)).  Given g = dL/dTheta (device double[npix], same pixel
+ * selection), writes grad_out = device double[ngrad][ld_g] with rows dL/dX (3), dL/dXdot (3)
+ * and, when ngrad = 9, dL/dX' (3), for every sample (dsigma held fixed).  Pair terms are
+ * recomputed, not stored; the reduction over pixels has a fixed order (deterministic). */
+int isw_map_adjoint(isw_ctx *ctx, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list,
+                    const double *samples, int64_t n, int64_t ld, const double *x_obs, double GU, int prec,
+                    const double *dL_dtheta, double *grad_out, int64_t ld_g, int ngrad, void *stream);
+
+/* Many shells into one full-sky map (Sec. III.A: the final map is the sum of maps sourced
+ * by subsets of the simulation cones).  nodes: device double[10][ld] of all shells
+ * concatenated; shell_off: host int64[nshell+1] offsets; t_box, mode: host arrays of
+ * nshell; loop_params as in lightcone_intersect.  The light-cone solve of every shell and
+ * one map over all samples are enqueued (flags: ISW_SKIP_LIGHTCONE when nodes are already
+ * samples on the cone; ISW_GRAPH to capture the sequence in a CUDA graph that later calls
+ * with the same arguments replay; ISW_AUTOTUNE to pick the FP32 kernel variant by timing).
+ * theta_out: device double[12 N^2] (RING), written or accumulated as in isw_map. */
+int isw_map_batched(isw_ctx *ctx, int64_t nside, const double *nodes, int64_t ld, const int64_t *shell_off,
+                    int64_t nshell, const double *t_box, const int32_t *mode, const double *loop_params,
+                    int64_t nloops, int64_t ldp, const double *x_obs, double t_obs, double GU, int prec,
+                    int flags, int accumulate, double *theta_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISW_H */

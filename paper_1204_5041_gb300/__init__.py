@@ -1,0 +1,336 @@
+"""GB300-native full-sky string ISW maps (Eq. 1-2 of arXiv:1204.5041) -- Python binding.
+
+A thin ctypes layer over the C ABI of ``libisw.so`` (include/isw.h): it only marshals
+PyTorch CUDA tensors into device pointers and the current CUDA stream; every step of the
+computation runs in the library's kernels.  If the library cannot be loaded the calls
+raise -- there is no CPU fallback.
+
+Functions carry the names of the C entry points:
+  hp_pix2vec_ring, lightcone_intersect, isw_map, isw_map_adjoint, isw_map_batched,
+and ``ISWMap`` is the ``torch.autograd.Function`` (forward = isw_map, backward =
+isw_map_adjoint).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "build", "Context", "default_context", "hp_pix2vec_ring", "lightcone_intersect", "isw_map",
+    "isw_map_adjoint", "isw_map_batched", "ISWMap", "ISWError", "F64", "F32C", "LINEAR", "BURDEN",
+]
+
+OK, EINVAL, ECUDA, EDOMAIN, ENOCONV, ETIMEOUT, ENOMEM = range(7)
+F64, F32C = 0, 1
+LINEAR, BURDEN = 0, 1
+SKIP_LIGHTCONE, GRAPH, AUTOTUNE = 1, 2, 4
+PARAM_NEAR_K, PARAM_B_MIN, PARAM_SPLIT, PARAM_VARIANT, PARAM_TIMING = range(5)
+_STATUS_NAMES = {0: "ISW_OK", 1: "ISW_EINVAL", 2: "ISW_ECUDA", 3: "ISW_EDOMAIN", 4: "ISW_ENOCONV",
+                 5: "ISW_ETIMEOUT", 6: "ISW_ENOMEM"}
+
+_lib = None
+_lib_lock = threading.Lock()
+_vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+
+
+class ISWError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile libisw.so for sm_103a (in-tree)."""
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded libisw.so (built on first use if the toolkit is present)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
+            L = ctypes.CDLL(path)
+            sig = {
+                "isw_create": (_i32, [ctypes.POINTER(_vp), _i32]),
+                "isw_destroy": (_i32, [_vp]),
+                "isw_last_error": (ctypes.c_char_p, [_vp]),
+                "isw_check_status": (_i32, [_vp, _vp, ctypes.POINTER(_i64)]),
+                "isw_set_param": (_i32, [_vp, _i32, _dbl]),
+                "isw_get_timing": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                          _i32]),
+                "hp_pix2vec_ring": (_i32, [_vp, _i64, _i64, _i64, _vp, _vp, _i64, _vp]),
+                "lightcone_intersect": (_i32, [_vp, _i32, _vp, _i64, _i64, _vp, _i64, _i64, _dbl, _vp, _dbl,
+                                               _vp, _i64, _vp, _vp, _vp]),
+                "isw_map": (_i32, [_vp, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _dbl, _i32, _i32, _vp,
+                                   _vp]),
+                "isw_map_adjoint": (_i32, [_vp, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _dbl, _i32, _vp,
+                                           _vp, _i64, _i32, _vp]),
+                "isw_map_batched": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp,
+                                           _dbl, _dbl, _i32, _i32, _i32, _vp, _vp]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class Context:
+    """An ``isw_ctx`` bound to one CUDA device (workspace + device status word)."""
+
+    def __init__(self, device: int | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        self._h = _vp()
+        r = lib().isw_create(ctypes.byref(self._h), self.device)
+        if r != OK:
+            raise ISWError(r, f"isw_create(device={self.device}) failed")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().isw_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return (lib().isw_last_error(self._h) or b"").decode()
+
+    def check(self, r: int):
+        if r != OK:
+            raise ISWError(r, self.last_error())
+
+    def set_param(self, key: int, value: float):
+        self.check(lib().isw_set_param(self._h, int(key), float(value)))
+
+    def timing(self, reset: bool = True):
+        """(summed device ms of the timed pair-kernel launches, pair-kernel launches, all kernel
+        launches) since the last reset; device times need PARAM_TIMING on."""
+        ms, n, m = _dbl(), _i64(), _i64()
+        self.check(lib().isw_get_timing(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(m), int(reset)))
+        return ms.value, n.value, m.value
+
+    def check_status(self, stream=None, raise_on_error: bool = False):
+        """Synchronise the stream; return (status code, counts dict) and clear the device status."""
+        counts = (_i64 * 3)()
+        r = lib().isw_check_status(self._h, _stream(stream), counts)
+        if raise_on_error and r != OK:
+            raise ISWError(r, self.last_error())
+        return r, {"zero_pairs": counts[0], "skipped_samples": counts[1], "near_pairs": counts[2]}
+
+
+_contexts: dict[int, Context] = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _contexts:
+        _contexts[device] = Context(device)
+    return _contexts[device]
+
+
+def _stream(stream):
+    if stream is None:
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return _vp(stream.cuda_stream)
+    return _vp(int(stream))
+
+
+def _ptr(t):
+    return _vp(t.data_ptr()) if t is not None else _vp(0)
+
+
+def _dev_tensor(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t
+
+
+def _rows(t, nrows, name):
+    """A [nrows, n] tensor with unit stride along n -> (tensor, n, ld)."""
+    if t.dim() != 2 or t.shape[0] != nrows:
+        raise ValueError(f"{name} must have shape [{nrows}, n]")
+    if t.shape[1] > 0 and t.stride(1) != 1:
+        raise ValueError(f"{name} must have unit stride along its last axis")
+    n = t.shape[1]
+    ld = t.stride(0) if nrows > 1 else max(n, 1)
+    return n, max(ld, n)
+
+
+def _xobs(x_obs):
+    x = (0.0, 0.0, 0.0) if x_obs is None else tuple(float(v) for v in x_obs)
+    return (_dbl * 3)(*x)
+
+
+def _ctx(ctx):
+    return ctx if ctx is not None else default_context()
+
+
+def _precision(prec) -> int:
+    if prec in (F64, "f64", "fp64", torch.float64):
+        return F64
+    if prec in (F32C, "f32c", "fp32c", torch.float32):
+        return F32C
+    raise ValueError(f"unknown precision {prec!r}")
+
+
+def _pixels(nside, pix, pix0, npix):
+    if pix is not None:
+        pix = _dev_tensor(pix, torch.int64, "pix").contiguous()
+        return pix, 0, pix.numel()
+    if npix is None:
+        npix = 12 * nside * nside - pix0
+    return None, int(pix0), int(npix)
+
+
+def hp_pix2vec_ring(nside: int, pix=None, pix0: int = 0, npix: int | None = None, out=None, ctx=None,
+                    stream=None, device=None):
+    """RING pixel centres as a float64 CUDA tensor [3, npix]."""
+    c = _ctx(ctx)
+    pix, pix0, npix = _pixels(nside, pix, pix0, npix)
+    if out is None:
+        out = torch.empty((3, npix), dtype=torch.float64, device=device or f"cuda:{c.device}")
+    _dev_tensor(out, torch.float64, "out")
+    n, ld = _rows(out, 3, "out")
+    c.check(lib().hp_pix2vec_ring(c.handle, int(nside), pix0, npix, _ptr(pix), _ptr(out), ld, _stream(stream)))
+    return out
+
+
+def lightcone_intersect(mode: int, nodes, loop_params=None, t_box: float = 0.0, x_obs=None, t_obs: float = 1.0,
+                        out=None, tau=None, status=None, ctx=None, stream=None):
+    """Samples on the observer's past light cone: float64 CUDA tensor [10, n] (and tau, status if given)."""
+    c = _ctx(ctx)
+    _dev_tensor(nodes, torch.float64, "nodes")
+    n, ld = _rows(nodes, 10, "nodes")
+    if out is None:
+        out = torch.empty((10, n), dtype=torch.float64, device=nodes.device)
+    n2, ld_out = _rows(out, 10, "out")
+    if n2 != n:
+        raise ValueError("out must have as many columns as nodes")
+    P, nloops, ldp = None, 0, 0
+    if loop_params is not None:
+        _dev_tensor(loop_params, torch.float64, "loop_params")
+        nloops, ldp = _rows(loop_params, 17, "loop_params")
+        P = loop_params
+    if tau is not None:
+        _dev_tensor(tau, torch.float64, "tau")
+    if status is not None:
+        _dev_tensor(status, torch.int32, "status")
+    c.check(lib().lightcone_intersect(c.handle, int(mode), _ptr(nodes), n, ld, _ptr(P), nloops, ldp, float(t_box),
+                                      _xobs(x_obs), float(t_obs), _ptr(out), ld_out, _ptr(tau), _ptr(status),
+                                      _stream(stream)))
+    return out
+
+
+def isw_map(nside: int, samples, pix=None, pix0: int = 0, npix: int | None = None, x_obs=None, GU: float = 1.0,
+            prec="f32c", accumulate: bool = False, out=None, ctx=None, stream=None):
+    """Theta of Eq. (1)-(2) at the selected pixels: float64 CUDA tensor [npix]."""
+    c = _ctx(ctx)
+    _dev_tensor(samples, torch.float64, "samples")
+    n, ld = _rows(samples, 10, "samples")
+    pix, pix0, npix = _pixels(nside, pix, pix0, npix)
+    if out is None:
+        out = torch.empty(npix, dtype=torch.float64, device=samples.device)
+    _dev_tensor(out, torch.float64, "out")
+    if out.numel() != npix or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 tensor of npix elements")
+    c.check(lib().isw_map(c.handle, int(nside), pix0, npix, _ptr(pix), _ptr(samples), n, ld, _xobs(x_obs),
+                          float(GU), _precision(prec), int(bool(accumulate)), _ptr(out), _stream(stream)))
+    return out
+
+
+def isw_map_adjoint(nside: int, samples, dL_dtheta, pix=None, pix0: int = 0, npix: int | None = None, x_obs=None,
+                    GU: float = 1.0, prec="f32c", ngrad: int = 6, out=None, ctx=None, stream=None):
+    """dL/dX, dL/dXdot (and dL/dX' when ngrad = 9) per sample: float64 CUDA tensor [ngrad, n]."""
+    c = _ctx(ctx)
+    _dev_tensor(samples, torch.float64, "samples")
+    n, ld = _rows(samples, 10, "samples")
+    pix, pix0, npix = _pixels(nside, pix, pix0, npix)
+    _dev_tensor(dL_dtheta, torch.float64, "dL_dtheta")
+    g = dL_dtheta.contiguous()
+    if g.numel() != npix:
+        raise ValueError("dL_dtheta must have one value per selected pixel")
+    if ngrad not in (6, 9):
+        raise ValueError("ngrad must be 6 or 9")
+    if out is None:
+        out = torch.empty((ngrad, n), dtype=torch.float64, device=samples.device)
+    _dev_tensor(out, torch.float64, "out")
+    _, ld_g = _rows(out, ngrad, "out")
+    c.check(lib().isw_map_adjoint(c.handle, int(nside), pix0, npix, _ptr(pix), _ptr(samples), n, ld, _xobs(x_obs),
+                                  float(GU), _precision(prec), _ptr(g), _ptr(out), ld_g, int(ngrad),
+                                  _stream(stream)))
+    return out
+
+
+def isw_map_batched(nside: int, nodes, shell_off, t_box, mode, loop_params=None, x_obs=None, t_obs: float = 1.0,
+                    GU: float = 1.0, prec="f32c", flags: int = 0, accumulate: bool = False, out=None, ctx=None,
+                    stream=None):
+    """One full-sky RING map summed over many shells (host shell metadata, device nodes)."""
+    import numpy as np
+
+    c = _ctx(ctx)
+    _dev_tensor(nodes, torch.float64, "nodes")
+    n, ld = _rows(nodes, 10, "nodes")
+    off = np.ascontiguousarray(np.asarray(shell_off, dtype=np.int64))
+    tb = np.ascontiguousarray(np.asarray(t_box, dtype=np.float64))
+    md = np.ascontiguousarray(np.asarray(mode, dtype=np.int32))
+    nshell = len(tb)
+    if off.size != nshell + 1 or md.size != nshell or off[-1] != n:
+        raise ValueError("shell_off must have nshell + 1 entries ending at n; t_box, mode nshell entries")
+    P, nloops, ldp = None, 0, 0
+    if loop_params is not None:
+        _dev_tensor(loop_params, torch.float64, "loop_params")
+        nloops, ldp = _rows(loop_params, 17, "loop_params")
+        P = loop_params
+    npix = 12 * nside * nside
+    if out is None:
+        out = torch.empty(npix, dtype=torch.float64, device=nodes.device)
+    _dev_tensor(out, torch.float64, "out")
+    c.check(lib().isw_map_batched(c.handle, int(nside), _ptr(nodes), ld, off.ctypes.data_as(_vp), nshell,
+                                  tb.ctypes.data_as(_vp), md.ctypes.data_as(_vp), _ptr(P), nloops, ldp, _xobs(x_obs),
+                                  float(t_obs), float(GU), _precision(prec), int(flags), int(bool(accumulate)),
+                                  _ptr(out), _stream(stream)))
+    return out
+
+
+class ISWMap(torch.autograd.Function):
+    """Theta = isw_map(samples); backward returns dL/dsamples with rows X, Xdot (and X' if
+    ``ngrad`` = 9) from isw_map_adjoint; the dsigma row gets no gradient."""
+
+    @staticmethod
+    def forward(ctx, samples, nside, pix=None, x_obs=None, GU=1.0, prec="f32c", ngrad=6):
+        ctx.save_for_backward(samples, pix)
+        ctx.args = (nside, x_obs, GU, prec, ngrad)
+        return isw_map(nside, samples.detach(), pix=pix, x_obs=x_obs, GU=GU, prec=prec)
+
+    @staticmethod
+    def backward(ctx, grad_theta):
+        samples, pix = ctx.saved_tensors
+        nside, x_obs, GU, prec, ngrad = ctx.args
+        g = isw_map_adjoint(nside, samples.detach(), grad_theta.contiguous().to(torch.float64), pix=pix,
+                            x_obs=x_obs, GU=GU, prec=prec, ngrad=ngrad)
+        grad = torch.zeros_like(samples)
+        grad[:ngrad] = g
+        return grad, None, None, None, None, None, None

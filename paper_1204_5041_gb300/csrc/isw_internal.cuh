@@ -1,0 +1,318 @@
+// Internal declarations of the GB300 string-ISW library: device helpers shared by the
+// kernels (IEEE-explicit FP64 arithmetic, the angle routines, the HEALPix RING geometry,
+// mbarrier / bulk-copy wrappers) and the host-side context.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/isw.h"
+
+namespace isw {
+
+// ------------------------------------------------------------------------------------
+// FP64 with explicit IEEE rounding (no contraction into FMA): the pixel directions and the
+// light-cone solve are specified operation by operation so that they are reproducible.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+
+// pi rounded to the nearest double
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// sin and cos of x = f * pi/4, f in [0, 1]: Taylor series, ten terms after the first, each
+// term obtained from the previous one by (term * x^2) / ((2k)(2k+1)) (sin) or
+// / ((2k-1)(2k)) (cos), summed from the smallest term up.
+__device__ __forceinline__ void sincos_octant(double f, double &s, double &c)
+{
+    const double quarter_pi = kPi * 0.25;
+    const double x = dmul(f, quarter_pi);
+    const double x2 = dmul(x, x);
+    double st[11], ct[11];
+    st[0] = x;
+    ct[0] = 1.0;
+#pragma unroll
+    for (int k = 1; k <= 10; ++k) {
+        st[k] = ddiv(dmul(st[k - 1], x2), (double)((2 * k) * (2 * k + 1)));
+        ct[k] = ddiv(dmul(ct[k - 1], x2), (double)((2 * k - 1) * (2 * k)));
+    }
+    double S = 0.0, C = 0.0;
+#pragma unroll
+    for (int k = 10; k >= 0; --k) {
+        if (k & 1) {
+            S = dsub(S, st[k]);
+            C = dsub(C, ct[k]);
+        } else {
+            S = dadd(S, st[k]);
+            C = dadd(C, ct[k]);
+        }
+    }
+    s = S;
+    c = C;
+}
+
+// (sin, cos) of k*pi/4 + the folded octant angle
+__device__ __forceinline__ void octant_unfold(int k, double sf, double cf, double &s, double &c)
+{
+    switch (k & 7) {
+    case 0: s = sf;  c = cf;  break;
+    case 1: s = cf;  c = sf;  break;
+    case 2: s = cf;  c = -sf; break;
+    case 3: s = sf;  c = -cf; break;
+    case 4: s = -sf; c = -cf; break;
+    case 5: s = -cf; c = -sf; break;
+    case 6: s = -cf; c = sf;  break;
+    default: s = -sf; c = cf; break;
+    }
+}
+
+// sin and cos of pi*a/b, b > 0, with the angle reduced exactly in integers
+__device__ __forceinline__ void sincospi_frac(int64_t a, int64_t b, double &s, double &c)
+{
+    const int64_t m = 8 * b;
+    int64_t A = (4 * a) % m;
+    if (A < 0) A += m;
+    const int64_t k = A / b;
+    const int64_t r = A - k * b;
+    const double f = (k & 1) ? ddiv((double)(b - r), (double)b) : ddiv((double)r, (double)b);
+    double sf, cf;
+    sincos_octant(f, sf, cf);
+    octant_unfold((int)k, sf, cf, s, c);
+}
+
+// sin and cos of 2*pi*w, reduced in turns (exact for |w| < 2^52)
+__device__ __forceinline__ void sincos_turns(double w, double &s, double &c)
+{
+    double wr = dsub(w, floor(w));
+    if (wr >= 1.0) wr = 0.0;
+    const double e = dmul(wr, 8.0);
+    const double kd = floor(e);
+    const double r = dsub(e, kd);
+    const int k = (int)kd;
+    const double f = (k & 1) ? dsub(1.0, r) : r;
+    double sf, cf;
+    sincos_octant(f, sf, cf);
+    octant_unfold(k, sf, cf, s, c);
+}
+
+__device__ __forceinline__ int64_t isqrt64(int64_t v)
+{
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r > 0 && r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+// Centre of RING pixel p at resolution N (HEALPix geometry, Gorski et al. 2005): rings
+// i = 1..4N-1 from the north; polar caps hold 4i pixels at z = +-(1 - i^2/(3N^2)),
+// phi = pi (2j-1)/(4i); the belt holds 4N pixels at z = (4N - 2i)/(3N),
+// phi = pi (2j - s)/(4N), s = 2 when i + N is odd, 1 when even.
+__device__ __forceinline__ void pix2vec_ring(int64_t N, int64_t p, double &x, double &y, double &z)
+{
+    const int64_t npix = 12 * N * N;
+    const int64_t ncap = 2 * N * (N - 1);
+    int64_t i, j, a, b;
+    double st;
+    if (p < ncap) {
+        i = (1 + isqrt64(1 + 2 * p)) / 2;
+        j = p - 2 * i * (i - 1) + 1;
+        z = ddiv((double)(3 * N * N - i * i), (double)(3 * N * N));
+        st = ddiv(dmul((double)i, dsqrt((double)(6 * N * N - i * i))), (double)(3 * N * N));
+        a = 2 * j - 1;
+        b = 4 * i;
+    } else if (p < npix - ncap) {
+        const int64_t q = p - ncap;
+        i = q / (4 * N) + N;
+        j = q % (4 * N) + 1;
+        const int64_t s = ((i + N) & 1) ? 2 : 1;
+        z = ddiv((double)(4 * N - 2 * i), (double)(3 * N));
+        st = ddiv(dsqrt((double)((2 * i - N) * (7 * N - 2 * i))), (double)(3 * N));
+        a = 2 * j - s;
+        b = 4 * N;
+    } else {
+        const int64_t q = npix - p;
+        i = (1 + isqrt64(2 * q - 1)) / 2;
+        j = 4 * i + 1 - (q - 2 * i * (i - 1));
+        z = -ddiv((double)(3 * N * N - i * i), (double)(3 * N * N));
+        st = ddiv(dmul((double)i, dsqrt((double)(6 * N * N - i * i))), (double)(3 * N * N));
+        a = 2 * j - 1;
+        b = 4 * i;
+    }
+    double sp, cp;
+    sincospi_frac(a, b, sp, cp);
+    x = dmul(st, cp);
+    y = dmul(st, sp);
+}
+
+// RING index of the pixel at (ix, iy) of base face f (0..11): the twelve base pixels are
+// rhombi; face f spans rings around jr(f)*N, with jr = 2 (north faces 0-3), 3 (equatorial
+// faces 4-7), 4 (south faces 8-11), and its corner sits at longitude jp(f) * pi/4.
+// Used only to order pixels in compact 2-D tiles; any bijection gives the same map.
+__device__ __forceinline__ int64_t xyf2ring(int64_t N, int f, int64_t ix, int64_t iy)
+{
+    const int jr_face = (f < 4) ? 2 : (f < 8 ? 3 : 4);
+    const int jp_face = (f < 4) ? 2 * f + 1 : (f < 8 ? 2 * (f - 4) : 2 * (f - 8) + 1);
+    const int64_t jr = (int64_t)jr_face * N - ix - iy - 1;
+    const int64_t npix = 12 * N * N;
+    const int64_t ncap = 2 * N * (N - 1);
+    int64_t nr, before, kshift;
+    if (jr < N) {
+        nr = jr;
+        before = 2 * nr * (nr - 1);
+        kshift = 0;
+    } else if (jr > 3 * N) {
+        nr = 4 * N - jr;
+        before = npix - 2 * nr * (nr + 1);
+        kshift = 0;
+    } else {
+        nr = N;
+        before = ncap + (jr - N) * 4 * N;
+        kshift = (jr - N) & 1;
+    }
+    // floor division: the numerator is negative on face 4 (corner at longitude 0), so shift it
+    // by 8 nr (even) before dividing
+    int64_t jp = ((int64_t)jp_face * nr + ix - iy + 1 + kshift + 8 * nr) / 2 - 4 * nr;
+    if (jp > 4 * nr) jp -= 4 * nr;
+    if (jp < 1) jp += 4 * nr;
+    return before + jp - 1;
+}
+
+// ------------------------------------------------------------------------------------
+// mbarrier + 1-D bulk copy (TMA engine) wrappers.  Waits are bounded: a wait that runs
+// out returns false and the caller reports ISW_ETIMEOUT instead of spinning forever.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity`; about 2^22 polls (each try_wait itself blocks for a
+// hardware-defined interval) before giving up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+    }
+    return false;
+}
+
+// global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned),
+// completion signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Device-side error reporting: status bits OR-ed into a word the host reads on demand.
+enum : uint32_t {
+    kStatDomain = 1u << 0,   // a segment with 1 - Xdot^2 <= 0 or a non-finite weight
+    kStatTimeout = 1u << 1,  // a bounded wait ran out
+    kStatNoConv = 1u << 2,   // light-cone Newton iteration cap reached
+    kStatBadIndex = 1u << 3, // a loop id or pixel index out of range
+};
+
+struct DevStatus {
+    uint32_t bits;
+    uint32_t pad;
+    unsigned long long zero_pairs;   // D = 0 pairs (zero contribution)
+    unsigned long long domain_segs;  // skipped segments
+    unsigned long long near_pairs;   // pairs evaluated in FP64 by the FP32 path
+};
+
+// ------------------------------------------------------------------------------------
+// Packed segment records.
+// FP32 record (64 B): Xhat hi (3), c, Xhat lo (3), rho^2, Xdot (3), 1 - |Xdot|, X' (3), 0
+// with c = -4 GU eps dsigma / |X|, rho = near-field chord radius.
+// FP64 record (128 B): Xhat hi (3), Xhat lo (3), Xdot (3), X' (3), c, 1 - |Xdot|, 0, 0.
+// Segment tile cap (32 B): centre (3), chord radius, max rho, min (1 - |Xdot|), 0, 0.
+// Pixel tile cap (16 B): centre (3), chord radius.
+// ------------------------------------------------------------------------------------
+struct __align__(16) Seg32 {
+    float4 a, b, d, e;
+};
+struct __align__(16) Seg64 {
+    double xh[3], xl[3], xd[3], xp[3], c, om, pad0, pad1;
+};
+struct __align__(16) SegCap {
+    float4 c;   // centre xyz, chord radius
+    float4 r;   // rho_max, om_min, -, -
+};
+
+struct Tunables {
+    int threads;    // threads per CTA (FP32 map)
+    int ppt;        // pixels per thread
+    int seg_tile;   // segments per shared-memory tile
+    int split;      // segment chunks (0 = automatic)
+};
+
+}  // namespace isw
+
+// ------------------------------------------------------------------------------------
+// Host-side context
+// ------------------------------------------------------------------------------------
+struct isw_ctx {
+    int device;
+    int num_sms;
+    char last_error[512];
+    isw::DevStatus *d_status;     // device status word + counters
+    // workspace buffers (grown on demand, never shrunk)
+    void *ws[8];
+    size_t ws_size[8];
+    // tunables
+    double near_k;      // near-field radius in units of max(pixel size, segment angle)
+    double b_min;       // 1 + n.Xdot below this goes to FP64
+    int split_override; // segment chunks for the forward maps (0 = automatic)
+    int tile_override;  // FP32 kernel variant index (-1 = automatic)
+    int timeout_polls;  // reserved
+    // pair-kernel timing (ISW_PARAM_TIMING)
+    int timing;
+    int n_timed;
+    int64_t n_pair;     // pair-kernel launches since the last reset
+    int64_t n_launch;   // all kernel launches since the last reset
+    cudaEvent_t *ev;    // 2 * kMaxTimed events, created on first use
+};
+constexpr int kMaxTimed = 4096;

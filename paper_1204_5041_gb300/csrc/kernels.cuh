@@ -1,0 +1,64 @@
+// Launchers of the library's kernels (one translation unit each), called by the C ABI layer.
+#pragma once
+
+#include "isw_internal.cuh"
+
+namespace isw {
+
+// healpix.cu
+int launch_pix2vec(int64_t N, int64_t pix0, int64_t npix, const int64_t *pix_list, double *out, int64_t ld,
+                   DevStatus *st, cudaStream_t s);
+void launch_pixel_table(int64_t N, int mode, int64_t pix0, int64_t npix, const int64_t *pix_list, int tx, int ty,
+                        int64_t ntiles, double *nv, int64_t ldn, int64_t *outidx, float4 *caps, DevStatus *st,
+                        cudaStream_t s);
+
+// lightcone.cu
+void launch_lightcone(int mode, const double *nodes, int64_t n, int64_t ld, const double *P, int64_t nloops,
+                      int64_t ldp, double t_box, double xo0, double xo1, double xo2, double t_obs, double tol,
+                      int max_iter, double *out, int64_t ld_out, double *tau, int32_t *status, DevStatus *st,
+                      cudaStream_t s);
+// one launch over many shells: per-node shell lookup through shell_off (device copies)
+void launch_lightcone_shells(const double *nodes, int64_t n, int64_t ld, const int64_t *shell_off, int64_t nshell,
+                             const double *t_box, const int32_t *mode, const double *P, int64_t nloops, int64_t ldp,
+                             double xo0, double xo1, double xo2, double t_obs, double tol, double *out,
+                             int64_t ld_out, DevStatus *st, cudaStream_t s);
+
+// pack.cu: per-sample records of the map kernels and per-tile caps
+void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
+                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, DevStatus *st,
+                 cudaStream_t s);
+void launch_seg_caps(const Seg32 *s32, int64_t n, int64_t n_pad, int seg_tile, SegCap *caps, cudaStream_t s);
+
+// map.cu
+struct MapArgs {
+    const double *nv;        // pixel table directions [3][ldn]
+    int64_t ldn;
+    const int64_t *outidx;   // pixel table output indices
+    const float4 *pcaps;     // pixel tile caps
+    int64_t ntiles;          // pixel tiles
+    const Seg32 *s32;
+    const Seg64 *s64;
+    const SegCap *scaps;
+    int64_t nst;             // segment tiles
+    int split;               // segment chunks
+    float b_min;
+    double *theta;           // output (RING or list order)
+    double *partial;         // [split][ntiles*tile] when split > 1
+    int accumulate;
+    DevStatus *st;
+};
+struct Variant {
+    int threads, ppt, seg_tile, tx, ty;
+};
+int num_f32_variants();
+Variant f32_variant(int idx);
+int f64_seg_tile();
+Variant f64_variant();
+// slots = resident CTAs on the whole GPU for the variant
+int map_f32c_slots(int idx, int num_sms);
+int map_f64_slots(int num_sms);
+void launch_map_f32c(int idx, const MapArgs &a, int grid, cudaStream_t s);
+void launch_map_f64(const MapArgs &a, int grid, cudaStream_t s);
+void launch_reduce_partials(const MapArgs &a, int tile_sz, cudaStream_t s);
+
+}  // namespace isw

@@ -1,0 +1,205 @@
+// Per-sample records of the map kernels (FP64 in, FP32 + FP64 out) and per-tile caps.
+//
+// With D = X n - X_s = X (n - Xhat), X = |X_s - x_obs|, Eq. (1)-(2) per pair become
+//   t = c [ B (Xdot.d) - A (X'.d) ] / [ B (d.d) ],  d = n - Xhat,  A = n.X',  B = 1 + n.Xdot,
+//   c = -4 GU eps dsigma / X,  eps^2 = X'^2 / (1 - Xdot^2)  (text after Eq. 1).
+// Xhat is formed in double-double so that d keeps full relative accuracy when n is close
+// to Xhat (near a string d cancels); the FP32 record carries it as a float pair (hi, lo).
+#include "isw_internal.cuh"
+#include "kernels.cuh"
+
+namespace isw {
+
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+{
+    const double x = dadd(a, b);
+    const double bb = dsub(x, a);
+    e = dadd(dsub(a, dsub(x, bb)), dsub(b, bb));
+    s = x;
+}
+
+// exact product: p + e = a * b
+__device__ __forceinline__ void two_prod(double a, double b, double &p, double &e)
+{
+    p = dmul(a, b);
+    e = __fma_rn(a, b, -p);
+}
+
+// r / |r| as hi + lo per component, and |r|
+__device__ __forceinline__ void unit_dd(const double r[3], double hi[3], double lo[3], double &norm)
+{
+    double sh = 0.0, sl = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double p, pe, s, se;
+        two_prod(r[k], r[k], p, pe);
+        two_sum(sh, p, s, se);
+        sl = dadd(sl, dadd(se, pe));
+        two_sum(s, sl, sh, sl);
+    }
+    const double q = dsqrt(sh);
+    double qq, qqe;
+    two_prod(q, q, qq, qqe);
+    const double ql = ddiv(dadd(dsub(dsub(sh, qq), qqe), sl), dmul(2.0, q));
+    double nh, nl;
+    two_sum(q, ql, nh, nl);
+    norm = nh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double q1 = ddiv(r[k], nh);
+        double p, pe;
+        two_prod(q1, nh, p, pe);
+        const double rem = dsub(dsub(dsub(r[k], p), pe), dmul(q1, nl));
+        const double q2 = ddiv(rem, nh);
+        two_sum(q1, q2, hi[k], lo[k]);
+    }
+}
+
+__global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, double xo0, double xo1, double xo2,
+                       double GU, double theta_pix, double near_k, int64_t n_pad, Seg32 *__restrict__ s32,
+                       Seg64 *__restrict__ s64, DevStatus *ds)
+{
+    unsigned long long bad = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
+        Seg64 g;
+        Seg32 f;
+        if (s < n) {
+            const double r[3] = {dsub(S[s], xo0), dsub(S[ld + s], xo1), dsub(S[2 * ld + s], xo2)};
+            double X;
+            unit_dd(r, g.xh, g.xl, X);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                g.xd[k] = S[(3 + k) * ld + s];
+                g.xp[k] = S[(6 + k) * ld + s];
+            }
+            const double dsig = S[9 * ld + s];
+            const double v2 = dadd(dadd(dmul(g.xd[0], g.xd[0]), dmul(g.xd[1], g.xd[1])), dmul(g.xd[2], g.xd[2]));
+            const double xp2 = dadd(dadd(dmul(g.xp[0], g.xp[0]), dmul(g.xp[1], g.xp[1])), dmul(g.xp[2], g.xp[2]));
+            const double om2 = dsub(1.0, v2);
+            const double eps = dsqrt(ddiv(xp2, om2));
+            const double w = dmul(eps, dsig);
+            double c = ddiv(dmul(-4.0 * GU, w), X);
+            const bool ok = (om2 > 0.0) && (X > 0.0) && isfinite(c);
+            if (!ok) {
+                c = 0.0;
+                ++bad;
+            }
+            g.c = c;
+            g.om = ok ? dsub(1.0, dsqrt(v2)) : 1.0;
+            // near-field chord radius: near_k * max(pixel size, angular length of the segment)
+            double ang = ok ? ddiv(w, X) : 0.0;
+            if (!(ang < 1.0)) ang = 1.0;
+            const double rho = near_k * fmax(theta_pix, ang);
+            float hi32[3], lo32[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                hi32[k] = __double2float_rn(g.xh[k]);
+                lo32[k] = __double2float_rn(dadd(dsub(g.xh[k], (double)hi32[k]), g.xl[k]));
+            }
+            f.a = make_float4(hi32[0], hi32[1], hi32[2], __double2float_rn(c));
+            f.b = make_float4(lo32[0], lo32[1], lo32[2], ok ? __double2float_rn(rho * rho) : -1.0f);
+            f.d = make_float4(__double2float_rn(g.xd[0]), __double2float_rn(g.xd[1]), __double2float_rn(g.xd[2]),
+                              __double2float_rn(g.om));
+            f.e = make_float4(__double2float_rn(g.xp[0]), __double2float_rn(g.xp[1]), __double2float_rn(g.xp[2]), 0.f);
+            if (!ok) {
+                // skipped sample: zero weight, moved to Xhat = 0 so every pair stays finite
+                f.a = make_float4(0.f, 0.f, 0.f, 0.f);
+                f.b = make_float4(0.f, 0.f, 0.f, -1.f);
+                f.d = make_float4(0.f, 0.f, 0.f, 1.f);
+                f.e = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int k = 0; k < 3; ++k) g.xh[k] = g.xl[k] = g.xd[k] = g.xp[k] = 0.0;
+            }
+        } else {
+            // padding: zero weight at Xhat = 0 (so d = n, d.d = 1), never near, B = 1
+            for (int k = 0; k < 3; ++k) g.xh[k] = g.xl[k] = g.xd[k] = g.xp[k] = 0.0;
+            g.c = 0.0;
+            g.om = 1.0;
+            f.a = make_float4(0.f, 0.f, 0.f, 0.f);
+            f.b = make_float4(0.f, 0.f, 0.f, -1.f);
+            f.d = make_float4(0.f, 0.f, 0.f, 1.f);
+            f.e = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        g.pad0 = g.pad1 = 0.0;
+        s32[s] = f;
+        s64[s] = g;
+    }
+    if (bad) {
+        atomicAdd(&ds->domain_segs, bad);
+        atomicOr(&ds->bits, kStatDomain);
+    }
+}
+
+// One warp per segment tile: centre of the Xhat directions, largest chord to it, largest
+// near radius and smallest 1 - |Xdot| over the tile's real samples.
+__global__ void k_seg_caps(const Seg32 *__restrict__ s32, int64_t n, int64_t n_pad, int seg_tile,
+                           SegCap *__restrict__ caps)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t ntile = n_pad / seg_tile;
+    if (warp >= ntile) return;
+    const int64_t base = warp * seg_tile;
+    float sx = 0.f, sy = 0.f, sz = 0.f, rho2 = 0.f, om = 1.f;
+    for (int l = lane; l < seg_tile; l += 32) {
+        const int64_t s = base + l;
+        const float4 b = s32[s < n ? s : 0].b;
+        if (s < n && b.w >= 0.f) {
+            const float4 a = s32[s].a, d = s32[s].d;
+            sx += a.x;
+            sy += a.y;
+            sz += a.z;
+            rho2 = fmaxf(rho2, b.w);
+            om = fminf(om, d.w);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        rho2 = fmaxf(rho2, __shfl_xor_sync(0xffffffffu, rho2, o));
+        om = fminf(om, __shfl_xor_sync(0xffffffffu, om, o));
+    }
+    const float nrm = sqrtf(sx * sx + sy * sy + sz * sz);
+    float cx = 0.f, cy = 0.f, cz = 1.f;
+    if (nrm > 0.f) {
+        cx = sx / nrm;
+        cy = sy / nrm;
+        cz = sz / nrm;
+    }
+    float r = 0.f;
+    for (int l = lane; l < seg_tile; l += 32) {
+        const int64_t s = base + l;
+        if (s < n && s32[s].b.w >= 0.f) {
+            const float4 a = s32[s].a;
+            const float dx = a.x - cx, dy = a.y - cy, dz = a.z - cz;
+            r = fmaxf(r, sqrtf(dx * dx + dy * dy + dz * dz));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) {
+        SegCap c;
+        c.c = make_float4(cx, cy, cz, r * 1.0001f + 1e-6f);
+        c.r = make_float4(sqrtf(rho2) * 1.0001f + 1e-6f, om, 0.f, 0.f);
+        caps[warp] = c;
+    }
+}
+
+void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
+                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, DevStatus *st,
+                 cudaStream_t s)
+{
+    if (n_pad <= 0) return;
+    int64_t blocks = (n_pad + 127) / 128;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_pack<<<(unsigned)blocks, 128, 0, s>>>(samples, n, ld, xo0, xo1, xo2, GU, theta_pix, near_k, n_pad, s32, s64, st);
+}
+
+void launch_seg_caps(const Seg32 *s32, int64_t n, int64_t n_pad, int seg_tile, SegCap *caps, cudaStream_t s)
+{
+    const int64_t ntile = n_pad / seg_tile;
+    if (ntile <= 0) return;
+    const int64_t threads = ntile * 32;
+    k_seg_caps<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(s32, n, n_pad, seg_tile, caps);
+}
+
+}  // namespace isw
