@@ -164,6 +164,28 @@ int isw_map_batched(isw_ctx *ctx, int64_t nside, const double *nodes, int64_t ld
                     int64_t nloops, int64_t ldp, const double *x_obs, double t_obs, double GU, int prec,
                     int flags, int accumulate, double *theta_out, void *stream);
 
+/* The FP32-compensated map of isw_map (full sky, or the RING range pix0 .. pix0+npix-1)
+ * for callers that may not allocate device memory: code running inside a host framework
+ * that owns all device memory through its own pool, or a latency-critical loop that cannot
+ * take the implicit device synchronisation of cudaMalloc / cudaFree.  The paper has no
+ * counterpart; this is a deployment variant of isw_map.
+ *   - Needs no isw_ctx and calls no cudaMalloc, cudaFree or allocating library routine.
+ *     Its scratch is a static device array of 64 MiB that every GPU loading the library
+ *     holds until the process exits; a problem whose scratch does not fit (roughly
+ *     40 bytes per padded pixel + 200 bytes per padded sample, e.g. a full Nside=256 sky
+ *     with 10^5 samples) is rejected with ISW_EINVAL before anything is enqueued.
+ *   - The first call on a device, with that device current, looks up the array's device
+ *     address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; each call clears
+ *     what must start at zero.  Calls that overlap on the GPU (for example on two streams
+ *     without ordering) race on the array and produce wrong maps.
+ *   - Arguments as in isw_map (device samples double[10][ld], device theta_out double[npix],
+ *     host x_obs or NULL); near-field and b_min settings are the defaults of isw_map.
+ *     Device-side conditions (skipped samples) are not reported; use isw_map with
+ *     isw_check_status to diagnose an input. */
+int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, const double *samples, int64_t n, int64_t ld,
+                         const double *x_obs, double GU, double *theta_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,162 @@
+// isw_map_f32c_noalloc: the FP32-compensated full map without any device allocation.
+//
+// Who needs it: callers that may not call cudaMalloc / cudaFree at all -- for example code
+// embedded in a host framework that owns all device memory through its own pool and forbids
+// raw CUDA allocations, or a latency-critical loop that cannot afford the implicit device
+// synchronisation cudaMalloc and cudaFree may perform.  isw_map needs an isw_ctx, whose
+// creation and workspace growth allocate; this entry point needs neither.
+//
+// Its scratch (pixel table, sample records, tile caps, segment-chunk partials and the
+// device status word) lives in one file-scope __device__ array of kStaticScratchBytes.
+// Every GPU that loads the library holds that array until the process exits.  All calls
+// share it and it keeps the previous call's contents: each call clears the status word and
+// overwrites every other byte it reads, and two calls that overlap on the GPU (different
+// streams, no ordering between them) race on it and give wrong maps.
+#include <cmath>
+#include <mutex>
+
+#include "isw_internal.cuh"
+#include "kernels.cuh"
+
+using namespace isw;
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB per device
+static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices];  // device address of g_scratch, per device
+int g_num_sms[kMaxDevices];
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// One-time set-up per device (the device must be current): the device address of the
+// static array.  In host code g_scratch names a host-side stand-in, never the device memory.
+int scratch_address(int dev, void **addr, int *sms)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ISW_ECUDA;
+        }
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return ISW_ECUDA;
+        g_num_sms[dev] = n;
+        g_scratch_addr[dev] = p;
+    }
+    *addr = g_scratch_addr[dev];
+    *sms = g_num_sms[dev];
+    return ISW_OK;
+}
+
+}  // namespace
+
+extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, const double *samples, int64_t n,
+                                    int64_t ld, const double *x_obs, double GU, double *theta_out, void *stream)
+{
+    // ---- host-side checks (nothing is enqueued when they fail)
+    if (nside < 1 || nside > (1 << 24)) return ISW_EINVAL;
+    const int64_t all = 12 * nside * nside;
+    if (npix < 0 || pix0 < 0 || pix0 + npix > all || n < 0 || (n > 0 && ld < n)) return ISW_EINVAL;
+    if (npix == 0) return ISW_OK;
+    if (!theta_out || (n > 0 && !samples)) return ISW_EINVAL;
+    if (!device_ptr(theta_out) || (n > 0 && !device_ptr(samples))) return ISW_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(theta_out, 0, (size_t)npix * sizeof(double), s) == cudaSuccess ? ISW_OK
+                                                                                                         : ISW_ECUDA;
+
+    // ---- scratch layout for the FP32 pair kernel's first variant
+    const Variant v = f32_variant(0);
+    const int S = v.seg_tile, tile = v.tx * v.ty;
+    const bool full = (pix0 == 0 && npix == all);
+    const int64_t ntiles = full ? 12 * ((nside + v.tx - 1) / v.tx) * ((nside + v.ty - 1) / v.ty)
+                                : (npix + tile - 1) / tile;
+    const int64_t tot = ntiles * tile;
+    const int64_t n_pad = (n + S - 1) / S * S, nst = n_pad / S;
+    size_t off[8];
+    size_t at = 0;
+    off[0] = at; at += up256(sizeof(DevStatus));
+    off[1] = at; at += up256((size_t)tot * 3 * sizeof(double));
+    off[2] = at; at += up256((size_t)tot * sizeof(int64_t));
+    off[3] = at; at += up256((size_t)ntiles * sizeof(float4));
+    off[4] = at; at += up256((size_t)n_pad * sizeof(Seg32));
+    off[5] = at; at += up256((size_t)n_pad * sizeof(Seg64));
+    off[6] = at; at += up256((size_t)nst * sizeof(SegCap));
+    off[7] = at;
+    if (at > kStaticScratchBytes) return ISW_EINVAL;  // problem too large for the static scratch
+    const int64_t room = (int64_t)((kStaticScratchBytes - at) / ((size_t)tot * sizeof(double)));
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ISW_ECUDA;
+    void *base = nullptr;
+    int sms = 0;
+    int r = scratch_address(dev, &base, &sms);
+    if (r) return r;
+
+    // segment chunks: fill the resident CTA slots in near-equal waves, within the scratch left
+    const int slots = map_f32c_slots(0, sms);
+    int split = 1;
+    double best = 1e300;
+    for (int k = 1; k <= 64 && k <= room; ++k) {
+        if (k > 1 && nst / k < 2) break;
+        const double t = (double)((ntiles * k + slots - 1) / slots) / k;
+        if (t < best * 0.98) {
+            best = t;
+            split = k;
+        }
+    }
+
+    unsigned char *b = (unsigned char *)base;
+    DevStatus *st = (DevStatus *)(b + off[0]);
+    double *nv = (double *)(b + off[1]);
+    int64_t *outidx = (int64_t *)(b + off[2]);
+    float4 *pcaps = (float4 *)(b + off[3]);
+    Seg32 *s32 = (Seg32 *)(b + off[4]);
+    Seg64 *s64 = (Seg64 *)(b + off[5]);
+    SegCap *scaps = (SegCap *)(b + off[6]);
+    double *partial = (double *)(b + off[7]);
+
+    // the status word is the only scratch read before it is written in this call
+    if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return ISW_ECUDA;
+    const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
+    const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
+    launch_pixel_table(nside, full ? 0 : 1, pix0, npix, nullptr, v.tx, v.ty, ntiles, nv, tot, outidx, pcaps, st, s);
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, s32, s64, st, s);
+    launch_seg_caps(s32, n, n_pad, S, scaps, s);
+    MapArgs a;
+    a.nv = nv;
+    a.ldn = tot;
+    a.outidx = outidx;
+    a.pcaps = pcaps;
+    a.ntiles = ntiles;
+    a.s32 = s32;
+    a.s64 = s64;
+    a.scaps = scaps;
+    a.nst = nst;
+    a.split = split;
+    a.b_min = 0.01f;
+    a.theta = theta_out;
+    a.partial = split > 1 ? partial : nullptr;
+    a.accumulate = 0;
+    a.st = st;
+    const int64_t items = ntiles * split;
+    launch_map_f32c(0, a, (int)(items < slots ? items : slots), s);
+    if (split > 1) launch_reduce_partials(a, tile, s);
+    return cudaGetLastError() == cudaSuccess ? ISW_OK : ISW_ECUDA;
+}
