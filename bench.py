@@ -133,7 +133,17 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=dev)
     # weak scaling: every rank maps its own independent string network (seed + rank)
     w = synth.config(1, seed=args.seed + rank)
+    if args.nside is not None:
+        w.nside = args.nside
     ctx = isw.default_context(local)
+    ctx.set_param(isw.PARAM_VARIANT, args.variant)
+    ctx.set_param(isw.PARAM_SPLIT, args.split)
+    if args.d_far is not None:
+        ctx.set_param(isw.PARAM_D_FAR, args.d_far)
+    if args.b_min is not None:
+        ctx.set_param(isw.PARAM_B_MIN, args.b_min)
+    if args.near_k is not None:
+        ctx.set_param(isw.PARAM_NEAR_K, args.near_k)
     nodes_h = torch.from_numpy(np.ascontiguousarray(w.nodes)).pin_memory()
     loops_h = torch.from_numpy(np.ascontiguousarray(w.loop_params)).pin_memory()
     loops_d = loops_h.to(dev)
@@ -325,6 +335,13 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
+    ap.add_argument("--variant", type=int, default=-1, help="FP32 pair-kernel variant (-1 = automatic)")
+    ap.add_argument("--split", type=int, default=0, help="segment chunks (0 = automatic)")
+    ap.add_argument("--d-far", type=float, default=None, help="far-field chord threshold (library default 0.4)")
+    ap.add_argument("--b-min", type=float, default=None, help="FP64 routing threshold on 1 + n.Xdot (default 0.01)")
+    ap.add_argument("--near-k", type=float, default=None, help="near-field radius factor (default 4)")
+    ap.add_argument("--nside", type=int, default=None,
+                    help="override the sky resolution (smaller skies for profiling; the bench line uses 512)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -61,7 +61,14 @@ enum { ISW_LINEAR = 0, ISW_BURDEN = 1 };
 /* isw_map_batched flags */
 enum { ISW_SKIP_LIGHTCONE = 1, ISW_GRAPH = 2, ISW_AUTOTUNE = 4 };
 /* isw_set_param keys */
-enum { ISW_PARAM_NEAR_K = 0, ISW_PARAM_B_MIN = 1, ISW_PARAM_SPLIT = 2, ISW_PARAM_VARIANT = 3, ISW_PARAM_TIMING = 4 };
+enum {
+    ISW_PARAM_NEAR_K = 0,
+    ISW_PARAM_B_MIN = 1,
+    ISW_PARAM_SPLIT = 2,
+    ISW_PARAM_VARIANT = 3,
+    ISW_PARAM_TIMING = 4,
+    ISW_PARAM_D_FAR = 5
+};
 
 /* Create a context bound to CUDA device `device`.  Allocates a small device status block.
  * Returns ISW_EINVAL for a bad device index, ISW_ECUDA / ISW_ENOMEM on CUDA failures. */
@@ -84,7 +91,10 @@ int isw_check_status(isw_ctx *ctx, void *stream, int64_t *counts);
  * below near_k * max(pixel size, angular length of the sample's segment); ISW_PARAM_B_MIN
  * (default 0.01): a pair with 1 + n.Xdot below b_min is evaluated in FP64 by the FP32 path;
  * ISW_PARAM_SPLIT: number of segment chunks of the forward maps (0 = automatic);
- * ISW_PARAM_VARIANT: FP32 kernel variant (-1 = automatic); ISW_PARAM_TIMING (default 0):
+ * ISW_PARAM_VARIANT: FP32 kernel variant (-1 = automatic); ISW_PARAM_D_FAR (default 0.4):
+ * segment tiles whose every pair is at least this chord apart from the pixel tile use the
+ * FP32 far-field form (d.d = 2 (1 - n.Xhat), Xdot.d and X'.d from per-sample constants);
+ * 4 disables it; ISW_PARAM_TIMING (default 0):
  * when 1, every launch of the pair kernel (the all-pairs sum of isw_map and
  * isw_map_batched) is bracketed by CUDA events on its stream, read by isw_get_timing. */
 int isw_set_param(isw_ctx *ctx, int key, double value);

@@ -211,7 +211,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, c->d_status, s);
     c->n_launch += 3;
     if (prec == ISW_F32C) {
-        launch_seg_caps(s32, n, n_pad, S, scaps, s);
+        launch_seg_caps(s32, s64, n, n_pad, S, (float)c->b_min, scaps, s);
         c->n_launch += 1;
     }
 
@@ -227,6 +227,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.nst = nst;
     a.split = split;
     a.b_min = (float)c->b_min;
+    a.d_far = (float)c->d_far;
     a.theta = theta;
     a.partial = split > 1 ? (double *)c->ws[kWsPartial] : nullptr;
     a.accumulate = accumulate;
@@ -264,6 +265,7 @@ int isw_create(isw_ctx **out, int device)
     c->device = device;
     c->near_k = 4.0;
     c->b_min = 0.01;
+    c->d_far = 0.4;
     c->split_override = 0;
     c->tile_override = -1;
     cudaError_t e = cudaSetDevice(device);
@@ -314,6 +316,10 @@ int isw_set_param(isw_ctx *c, int key, double value)
     case ISW_PARAM_SPLIT:
         if (!(value >= 0.0 && value <= 1024.0)) return set_err(c, ISW_EINVAL, "split out of range");
         c->split_override = (int)value;
+        return ISW_OK;
+    case ISW_PARAM_D_FAR:
+        if (!(value >= 0.0 && value <= 4.0)) return set_err(c, ISW_EINVAL, "d_far out of range");
+        c->d_far = value;
         return ISW_OK;
     case ISW_PARAM_TIMING:
         c->timing = value != 0.0;

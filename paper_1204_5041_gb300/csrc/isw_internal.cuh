@@ -265,14 +265,17 @@ struct DevStatus {
 
 // ------------------------------------------------------------------------------------
 // Packed segment records.
-// FP32 record (64 B): Xhat hi (3), c, Xhat lo (3), rho^2, Xdot (3), 1 - |Xdot|, X' (3), 0
-// with c = -4 GU eps dsigma / |X|, rho = near-field chord radius.
+// FP32 record (80 B): Xhat hi (3), c | Xhat lo (3), rho^2 | Xdot (3), e | X' (3), f |
+// Xdot/|Xdot| (3), 1 - |Xdot|, with c = -4 GU eps dsigma / |X|, rho = near-field chord
+// radius, e = 1 + Xdot.Xhat, f = X'.Xhat (so that Xdot.d = B - e and X'.d = A - f for
+// d = n - Xhat); the last four give B = (1 - |Xdot|) + |Xdot| |n + Xdot/|Xdot||^2 / 2
+// without cancellation when n approaches -Xdot/|Xdot|.
 // FP64 record (128 B): Xhat hi (3), Xhat lo (3), Xdot (3), X' (3), c, 1 - |Xdot|, 0, 0.
-// Segment tile cap (32 B): centre (3), chord radius, max rho, min (1 - |Xdot|), 0, 0.
+// Segment tile cap (48 B): centre (3), chord radius, max rho, min (1 - |Xdot|), beam cap (4).
 // Pixel tile cap (16 B): centre (3), chord radius.
 // ------------------------------------------------------------------------------------
 struct __align__(16) Seg32 {
-    float4 a, b, d, e;
+    float4 a, b, d, e, k;
 };
 struct __align__(16) Seg64 {
     double xh[3], xl[3], xd[3], xp[3], c, om, pad0, pad1;
@@ -280,6 +283,8 @@ struct __align__(16) Seg64 {
 struct __align__(16) SegCap {
     float4 c;   // centre xyz, chord radius
     float4 r;   // rho_max, om_min, -, -
+    float4 b;   // beam cap of the samples with 1 - |Xdot| < b_min: centre of -Xdot/|Xdot| (xyz) and
+                // chord radius enlarged by the B < b_min cone; radius < 0 when there is no such sample
 };
 
 struct Tunables {
@@ -305,6 +310,7 @@ struct isw_ctx {
     // tunables
     double near_k;      // near-field radius in units of max(pixel size, segment angle)
     double b_min;       // 1 + n.Xdot below this goes to FP64
+    double d_far;       // segment tiles this chord away from the pixel tile use the far-field form
     int split_override; // segment chunks for the forward maps (0 = automatic)
     int tile_override;  // FP32 kernel variant index (-1 = automatic)
     int timeout_polls;  // reserved

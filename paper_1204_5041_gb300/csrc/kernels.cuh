@@ -27,7 +27,8 @@ void launch_lightcone_shells(const double *nodes, int64_t n, int64_t ld, const i
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
                  double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, DevStatus *st,
                  cudaStream_t s);
-void launch_seg_caps(const Seg32 *s32, int64_t n, int64_t n_pad, int seg_tile, SegCap *caps, cudaStream_t s);
+void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
+                     SegCap *caps, cudaStream_t s);
 
 // map.cu
 struct MapArgs {
@@ -42,6 +43,7 @@ struct MapArgs {
     int64_t nst;             // segment tiles
     int split;               // segment chunks
     float b_min;
+    float d_far;             // tile pairs at least this chord apart use the far-field form
     double *theta;           // output (RING or list order)
     double *partial;         // [split][ntiles*tile] when split > 1
     int accumulate;

@@ -75,7 +75,7 @@ __device__ __forceinline__ void drain(uint64_t *bars, uint32_t g, int i, int nt)
 }
 
 template <int NT, int P, int S>
-__global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : 4)) k_map_f32c(MapArgs a)
+__global__ void __launch_bounds__(NT, (P >= 8 ? 1 : (NT >= 256 ? 2 : 4))) k_map_f32c(MapArgs a)
 {
     constexpr int TILE = NT * P;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -133,12 +133,35 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : 4)) k_map_f32c(MapArgs a)
                 const int64_t j = j0 + i;
                 const SegCap sc = a.scaps[j];
                 const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
-                const bool near = (sqrtf(ex * ex + ey * ey + ez * ez) < pc.w + sc.c.w + sc.r.x) || (sc.r.y < a.b_min);
+                const float gap = sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w;  // lower bound of |d|
+                // B = 1 + n.Xdot >= b_min for every pair unless the pixel cap meets the tile's beam cap
+                const float bx = pc.x - sc.b.x, by = pc.y - sc.b.y, bz = pc.z - sc.b.z;
+                const bool fast_b = sc.b.w < 0.f || sqrtf(bx * bx + by * by + bz * bz) > pc.w + sc.b.w;
+                const bool near = (gap < sc.r.x) || !fast_b;
+                const bool far = fast_b && (gap >= a.d_far);
                 const Seg32 *sb = sbuf + buf * S;
                 float part[P];
 #pragma unroll
                 for (int q = 0; q < P; ++q) part[q] = 0.f;
-                if (!near) {
+                if (far) {
+                    // |d| >= d_far for every pair: d.d/2 = 1 - n.Xhat, Xdot.d = B - e, X'.d = A - f
+#pragma unroll 2
+                    for (int s = 0; s < S; ++s) {
+                        const float4 ra = sb[s].a, rd = sb[s].d, re = sb[s].e;
+                        const float ch = 0.5f * ra.w;
+#pragma unroll
+                        for (int q = 0; q < P; ++q) {
+                            const float h = fmaf(-nh[q][2], ra.z, fmaf(-nh[q][1], ra.y, fmaf(-nh[q][0], ra.x, 1.f)));
+                            const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
+                            const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
+                            const float Pd = B - rd.w;
+                            const float Qd = A - re.w;
+                            const float num = fmaf(B, Pd, -A * Qd);
+                            const float r = rcp_approx(B * h);
+                            part[q] = fmaf(ch * num, r, part[q]);
+                        }
+                    }
+                } else if (!near) {
 #pragma unroll 2
                     for (int s = 0; s < S; ++s) {
                         const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e;
@@ -158,8 +181,12 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : 4)) k_map_f32c(MapArgs a)
                         }
                     }
                 } else {
+                    // checked loop: two-float d, B formed without cancellation near -Xdot/|Xdot|;
+                    // pairs with |d| < rho or B < b_min/1000 go to FP64
+                    const float b_tiny = a.b_min * 1e-3f;
                     for (int s = 0; s < S; ++s) {
-                        const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e;
+                        const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e, rk = sb[s].k;
+                        const float hv = fmaf(-0.5f, rk.w, 0.5f);   // |Xdot| / 2
                         unsigned mask = 0;
 #pragma unroll
                         for (int q = 0; q < P; ++q) {
@@ -170,8 +197,9 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 2 : 4)) k_map_f32c(MapArgs a)
                             const float Pd = fmaf(rd.z, dz, fmaf(rd.y, dy, rd.x * dx));
                             const float Qd = fmaf(re.z, dz, fmaf(re.y, dy, re.x * dx));
                             const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
-                            const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
-                            if (Q < rb.w || B < a.b_min) {
+                            const float wx = nh[q][0] + rk.x, wy = nh[q][1] + rk.y, wz = nh[q][2] + rk.z;
+                            const float B = fmaf(hv, fmaf(wz, wz, fmaf(wy, wy, wx * wx)), rk.w);
+                            if (Q < rb.w || B < b_tiny) {
                                 mask |= 1u << q;
                             } else {
                                 const float num = fmaf(B, Pd, -A * Qd);

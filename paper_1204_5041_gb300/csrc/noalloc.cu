@@ -138,7 +138,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     launch_pixel_table(nside, full ? 0 : 1, pix0, npix, nullptr, v.tx, v.ty, ntiles, nv, tot, outidx, pcaps, st, s);
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, s32, s64, st, s);
-    launch_seg_caps(s32, n, n_pad, S, scaps, s);
+    launch_seg_caps(s32, s64, n, n_pad, S, 0.01f, scaps, s);
     MapArgs a;
     a.nv = nv;
     a.ldn = tot;
@@ -151,6 +151,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.nst = nst;
     a.split = split;
     a.b_min = 0.01f;
+    a.d_far = 0.4f;
     a.theta = theta_out;
     a.partial = split > 1 ? partial : nullptr;
     a.accumulate = 0;

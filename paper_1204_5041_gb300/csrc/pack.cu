@@ -98,16 +98,28 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
             }
             f.a = make_float4(hi32[0], hi32[1], hi32[2], __double2float_rn(c));
             f.b = make_float4(lo32[0], lo32[1], lo32[2], ok ? __double2float_rn(rho * rho) : -1.0f);
+            // far-field constants: Xdot.d = B - e and X'.d = A - f with d = n - Xhat
+            const double e1 = dadd(1.0, dadd(dadd(dmul(g.xd[0], g.xh[0]), dmul(g.xd[1], g.xh[1])), dmul(g.xd[2], g.xh[2])));
+            const double f1 = dadd(dadd(dmul(g.xp[0], g.xh[0]), dmul(g.xp[1], g.xh[1])), dmul(g.xp[2], g.xh[2]));
             f.d = make_float4(__double2float_rn(g.xd[0]), __double2float_rn(g.xd[1]), __double2float_rn(g.xd[2]),
-                              __double2float_rn(g.om));
-            f.e = make_float4(__double2float_rn(g.xp[0]), __double2float_rn(g.xp[1]), __double2float_rn(g.xp[2]), 0.f);
+                              __double2float_rn(e1));
+            f.e = make_float4(__double2float_rn(g.xp[0]), __double2float_rn(g.xp[1]), __double2float_rn(g.xp[2]),
+                              __double2float_rn(f1));
+            {
+                const double v = dsqrt(v2);
+                const double iv = v > 0.0 ? ddiv(1.0, v) : 0.0;
+                f.k = make_float4(__double2float_rn(dmul(g.xd[0], iv)), __double2float_rn(dmul(g.xd[1], iv)),
+                                  __double2float_rn(dmul(g.xd[2], iv)), __double2float_rn(g.om));
+            }
             if (!ok) {
                 // skipped sample: zero weight, moved to Xhat = 0 so every pair stays finite
+                f.k = make_float4(0.f, 0.f, 0.f, 1.f);
                 f.a = make_float4(0.f, 0.f, 0.f, 0.f);
                 f.b = make_float4(0.f, 0.f, 0.f, -1.f);
                 f.d = make_float4(0.f, 0.f, 0.f, 1.f);
                 f.e = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int k = 0; k < 3; ++k) g.xh[k] = g.xl[k] = g.xd[k] = g.xp[k] = 0.0;
+                g.om = 1.0;
             }
         } else {
             // padding: zero weight at Xhat = 0 (so d = n, d.d = 1), never near, B = 1
@@ -118,6 +130,7 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
             f.b = make_float4(0.f, 0.f, 0.f, -1.f);
             f.d = make_float4(0.f, 0.f, 0.f, 1.f);
             f.e = make_float4(0.f, 0.f, 0.f, 0.f);
+            f.k = make_float4(0.f, 0.f, 0.f, 1.f);
         }
         g.pad0 = g.pad1 = 0.0;
         s32[s] = f;
@@ -131,8 +144,8 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
 
 // One warp per segment tile: centre of the Xhat directions, largest chord to it, largest
 // near radius and smallest 1 - |Xdot| over the tile's real samples.
-__global__ void k_seg_caps(const Seg32 *__restrict__ s32, int64_t n, int64_t n_pad, int seg_tile,
-                           SegCap *__restrict__ caps)
+__global__ void k_seg_caps(const Seg32 *__restrict__ s32, const Seg64 *__restrict__ s64, int64_t n, int64_t n_pad,
+                           int seg_tile, float b_min, SegCap *__restrict__ caps)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -144,12 +157,12 @@ __global__ void k_seg_caps(const Seg32 *__restrict__ s32, int64_t n, int64_t n_p
         const int64_t s = base + l;
         const float4 b = s32[s < n ? s : 0].b;
         if (s < n && b.w >= 0.f) {
-            const float4 a = s32[s].a, d = s32[s].d;
+            const float4 a = s32[s].a;
             sx += a.x;
             sy += a.y;
             sz += a.z;
             rho2 = fmaxf(rho2, b.w);
-            om = fminf(om, d.w);
+            om = fminf(om, (float)s64[s].om);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -176,10 +189,57 @@ __global__ void k_seg_caps(const Seg32 *__restrict__ s32, int64_t n, int64_t n_p
         }
     }
     for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    // beam cap: directions n with B = 1 + n.Xdot < b_min lie within chord sqrt(2 b_min / |Xdot|)
+    // of -Xdot/|Xdot|, and only samples with 1 - |Xdot| < b_min have any
+    float bx = 0.f, by = 0.f, bz = 0.f;
+    int nb = 0;
+    for (int l = lane; l < seg_tile; l += 32) {
+        const int64_t s = base + l;
+        if (s < n && s32[s].b.w >= 0.f && s64[s].om < (double)b_min) {
+            const float4 k = s32[s].k;
+            bx -= k.x;
+            by -= k.y;
+            bz -= k.z;
+            ++nb;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bx += __shfl_xor_sync(0xffffffffu, bx, o);
+        by += __shfl_xor_sync(0xffffffffu, by, o);
+        bz += __shfl_xor_sync(0xffffffffu, bz, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+    }
+    float4 beam = make_float4(0.f, 0.f, 1.f, -1.f);
+    if (nb > 0) {
+        const float bn = sqrtf(bx * bx + by * by + bz * bz);
+        if (bn > 0.f) {
+            bx /= bn;
+            by /= bn;
+            bz /= bn;
+        } else {
+            bx = 0.f;
+            by = 0.f;
+            bz = 1.f;
+        }
+        float rb = 0.f;
+        for (int l = lane; l < seg_tile; l += 32) {
+            const int64_t s = base + l;
+            if (s < n && s32[s].b.w >= 0.f && s64[s].om < (double)b_min) {
+                const float4 k = s32[s].k;
+                const float dx = -k.x - bx, dy = -k.y - by, dz = -k.z - bz;
+                rb = fmaxf(rb, sqrtf(dx * dx + dy * dy + dz * dz));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) rb = fmaxf(rb, __shfl_xor_sync(0xffffffffu, rb, o));
+        // |Xdot| > 1 - b_min for these samples; margin for FP32 rounding
+        const float cone = sqrtf(2.f * b_min / (1.f - b_min)) * 1.001f + 1e-5f;
+        beam = make_float4(bx, by, bz, rb * 1.0001f + cone);
+    }
     if (lane == 0) {
         SegCap c;
         c.c = make_float4(cx, cy, cz, r * 1.0001f + 1e-6f);
         c.r = make_float4(sqrtf(rho2) * 1.0001f + 1e-6f, om, 0.f, 0.f);
+        c.b = beam;
         caps[warp] = c;
     }
 }
@@ -194,12 +254,13 @@ void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, doubl
     k_pack<<<(unsigned)blocks, 128, 0, s>>>(samples, n, ld, xo0, xo1, xo2, GU, theta_pix, near_k, n_pad, s32, s64, st);
 }
 
-void launch_seg_caps(const Seg32 *s32, int64_t n, int64_t n_pad, int seg_tile, SegCap *caps, cudaStream_t s)
+void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
+                     SegCap *caps, cudaStream_t s)
 {
     const int64_t ntile = n_pad / seg_tile;
     if (ntile <= 0) return;
     const int64_t threads = ntile * 32;
-    k_seg_caps<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(s32, n, n_pad, seg_tile, caps);
+    k_seg_caps<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(s32, s64, n, n_pad, seg_tile, b_min, caps);
 }
 
 }  // namespace isw

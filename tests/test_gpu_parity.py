@@ -243,3 +243,33 @@ def test_map_nside512_200k_sampled(isw, cfg1, prec, tol):
     e = _err(got, ref)
     print(f"nside512 {prec}: max|d|/rms = {e:.3e} over {pix.size} pixels; counts {counts}")
     assert e <= tol
+
+
+def test_map_near_cusp_samples(isw):
+    """Samples with |Xdot| up to 1 - 1e-8 (beamed cusps): 1 + n.Xdot cancels for n near
+    -Xdot/|Xdot|; the FP32 path must still meet the bar there."""
+    rng = np.random.default_rng(17)
+    n = 2000
+    X = rng.normal(size=(3, n))
+    X *= 0.5 / np.linalg.norm(X, axis=0)
+    u = rng.normal(size=(3, n))
+    u /= np.linalg.norm(u, axis=0)
+    v = 1.0 - 10.0 ** rng.uniform(-8, -1, n)
+    p = rng.normal(size=(3, n))
+    p -= (p * u).sum(0) * u
+    p /= np.linalg.norm(p, axis=0)
+    S = np.zeros((10, n))
+    S[0:3] = X
+    S[3:6] = v * u
+    S[6:9] = np.sqrt(1.0 - v * v) * p
+    S[9] = 1e-3
+    N = 64
+    ref, _ = oracle.isw_map(N, S, threads=THREADS)
+    Sd = _d(S)
+    for prec, tol in (("f64", TOL64), ("f32c", TOL32)):
+        got = isw.isw_map(N, Sd, prec=prec).cpu().numpy()
+        r, counts = isw.default_context().check_status()
+        assert r == isw.OK
+        e = _err(got, ref)
+        print(f"near-cusp {prec}: max|d|/rms = {e:.3e}, counts {counts}")
+        assert e <= tol
