@@ -1,0 +1,426 @@
+// Adjoint of the map (an extension of the method): for a per-pixel g = dL/dTheta, the
+// gradient of L with respect to every sample's X, Xdot (and X'), by differentiating the pair
+// term of Eq. (1)-(2) and recomputing it pair by pair (nothing is stored per pair).
+//
+// With d = n - Xhat, Q = d.d, A = n.X', B = 1 + n.Xdot, u = Xdot - (A/B) X', c = -4GU eps dsig/X
+// and the pair term t = c T, T = (u.d)/Q, the derivatives of t are combinations of the
+// sample's own vectors Xhat, Xdot, X' and of n:
+//   dt/dX     = (c/X) [ alpha Xhat - Xdot/Q + (A/(BQ)) X' + eta n ],
+//                eta = 2 (u.d)/Q^2,  alpha = (u.Xhat)/Q - eta,
+//   dt/dXdot  = c [ T/(1 - Xdot^2) Xdot - Xhat/Q + (1 + A (X'.d)/B^2)/Q n ],
+//   dt/dX'    = c [ T/X'^2 X' + (A/(BQ)) Xhat - (X'.d + A)/(BQ) n ],
+// so a sample only accumulates four scalars and three n-weighted vectors over the pixels:
+//   S1 = sum g alpha, S2 = sum g/Q, S3 = sum g A/(BQ), S4 = sum g T,
+//   V1 = sum g eta n, V2 = sum g (1 + A (X'.d)/B^2)/Q n, V3 = sum g (X'.d + A)/(BQ) n,
+// and its gradient is assembled once, in FP64, from these sums and its FP64 record.
+//
+// Work items are (tile of NT samples, chunk of pixel tiles): one thread per sample, pixel
+// records of a tile staged in shared memory by 1-D bulk copies and read by every thread.
+// Per-chunk gradients are reduced over chunks in a fixed order (deterministic).
+#include "isw_internal.cuh"
+#include "kernels.cuh"
+#include "pipeline.cuh"
+
+namespace isw {
+
+constexpr int kAcc = 13;
+
+// FP64 pair derivative sums (used by the FP64 kernel and for the FP32 kernel's near field)
+__device__ __forceinline__ void adj_pair64(double nx, double ny, double nz, double g, const Seg64 &s, int ngrad,
+                                           double *acc, unsigned &zero)
+{
+    const double dx = (nx - s.xh[0]) - s.xl[0];
+    const double dy = (ny - s.xh[1]) - s.xl[1];
+    const double dz = (nz - s.xh[2]) - s.xl[2];
+    const double Q = dx * dx + dy * dy + dz * dz;
+    if (Q == 0.0) {
+        ++zero;
+        return;
+    }
+    const double A = nx * s.xp[0] + ny * s.xp[1] + nz * s.xp[2];
+    const double B = 1.0 + (nx * s.xd[0] + ny * s.xd[1] + nz * s.xd[2]);
+    const double Pd = s.xd[0] * dx + s.xd[1] * dy + s.xd[2] * dz;
+    const double Qd = s.xp[0] * dx + s.xp[1] * dy + s.xp[2] * dz;
+    const double uX = (s.xd[0] * s.xh[0] + s.xd[1] * s.xh[1] + s.xd[2] * s.xh[2]) -
+                      (A / B) * (s.xp[0] * s.xh[0] + s.xp[1] * s.xh[1] + s.xp[2] * s.xh[2]);
+    const double iQ = 1.0 / Q, iB = 1.0 / B;
+    const double AB = A * iB;
+    const double ud = Pd - AB * Qd;
+    const double T = ud * iQ;
+    const double eta = 2.0 * T * iQ;
+    const double alpha = uX * iQ - eta;
+    const double gq = g * iQ;
+    acc[0] += g * alpha;
+    acc[1] += gq;
+    acc[2] += gq * AB;
+    acc[3] += g * T;
+    const double ge = g * eta;
+    const double w2 = gq * (1.0 + AB * Qd * iB);
+    acc[4] += ge * nx;
+    acc[5] += ge * ny;
+    acc[6] += ge * nz;
+    acc[7] += w2 * nx;
+    acc[8] += w2 * ny;
+    acc[9] += w2 * nz;
+    if (ngrad == 9) {
+        const double w3 = gq * iB * (Qd + A);
+        acc[10] += w3 * nx;
+        acc[11] += w3 * ny;
+        acc[12] += w3 * nz;
+    }
+}
+
+// FP32 pair derivative sums from the pair quantities (shared by the far and checked loops)
+template <bool NG9>
+__device__ __forceinline__ void adj_pair32(float Q, float A, float B, float Pd, float Qd, float em1, float f,
+                                           float g, float nx, float ny, float nz, float *p)
+{
+    const float iQ = rcp_approx(Q), iB = rcp_approx(B);
+    const float AB = A * iB;
+    const float ud = fmaf(-AB, Qd, Pd);
+    const float T = ud * iQ;
+    const float eta = 2.f * T * iQ;
+    const float alpha = fmaf(fmaf(-AB, f, em1), iQ, -eta);
+    const float gq = g * iQ;
+    p[0] = fmaf(g, alpha, p[0]);
+    p[1] += gq;
+    p[2] = fmaf(gq, AB, p[2]);
+    p[3] = fmaf(g, T, p[3]);
+    const float ge = g * eta;
+    const float w2 = gq * fmaf(AB * Qd, iB, 1.f);
+    p[4] = fmaf(ge, nx, p[4]);
+    p[5] = fmaf(ge, ny, p[5]);
+    p[6] = fmaf(ge, nz, p[6]);
+    p[7] = fmaf(w2, nx, p[7]);
+    p[8] = fmaf(w2, ny, p[8]);
+    p[9] = fmaf(w2, nz, p[9]);
+    if (NG9) {
+        const float w3 = gq * iB * (Qd + A);
+        p[10] = fmaf(w3, nx, p[10]);
+        p[11] = fmaf(w3, ny, p[11]);
+        p[12] = fmaf(w3, nz, p[12]);
+    }
+}
+
+// Gradient rows of one sample from its sums (FP64)
+__device__ __forceinline__ void adj_assemble(const Seg64 &s, const double *acc, int ngrad, double *out)
+{
+    const double cX = s.c / s.X;
+    const double om2 = s.om * (2.0 - s.om);   // 1 - |Xdot|^2 = (1 - v)(1 + v)
+    const double xp2 = s.xp[0] * s.xp[0] + s.xp[1] * s.xp[1] + s.xp[2] * s.xp[2];
+    for (int k = 0; k < 3; ++k) {
+        const double xh = s.xh[k] + s.xl[k];
+        out[k] = cX * (acc[0] * xh - acc[1] * s.xd[k] + acc[2] * s.xp[k] + acc[4 + k]);
+        out[3 + k] = s.c * (acc[3] / om2 * s.xd[k] - acc[1] * xh + acc[7 + k]);
+        if (ngrad == 9) out[6 + k] = s.c * ((xp2 > 0.0 ? acc[3] / xp2 : 0.0) * s.xp[k] + acc[2] * xh - acc[10 + k]);
+    }
+}
+
+__global__ void k_pack_pixels(const double *__restrict__ nv, int64_t ldn, const int64_t *__restrict__ outidx,
+                              const double *__restrict__ g, int64_t tot, Pix32 *__restrict__ p32,
+                              Pix64 *__restrict__ p64)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < tot; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t oi = outidx[k];
+        Pix64 d;
+        Pix32 f;
+        if (oi >= 0) {
+            for (int c = 0; c < 3; ++c) d.n[c] = nv[c * ldn + k];
+            d.g = g[oi];
+        } else {
+            d.n[0] = d.n[1] = d.n[2] = 0.0;
+            d.g = 0.0;
+        }
+        float hi[3], lo[3];
+        for (int c = 0; c < 3; ++c) {
+            hi[c] = __double2float_rn(d.n[c]);
+            lo[c] = __double2float_rn(d.n[c] - (double)hi[c]);
+        }
+        f.a = make_float4(hi[0], hi[1], hi[2], __double2float_rn(d.g));
+        f.b = make_float4(lo[0], lo[1], lo[2], 0.f);
+        p32[k] = f;
+        p64[k] = d;
+    }
+}
+
+template <int NT, int TP, bool NG9>
+__global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    Pix32 *sbuf = reinterpret_cast<Pix32 *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * TP * sizeof(Pix32));
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    constexpr int NG = NG9 ? 9 : 6;
+    unsigned nearcnt = 0, zerocnt = 0;
+    uint32_t gl = 0;
+    const int64_t n_items = a.nseg_tiles * a.split;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t st = item / a.split;
+        const int kc = (int)(item - st * a.split);
+        const int64_t p0 = a.npix_tiles * kc / a.split, p1 = a.npix_tiles * (kc + 1) / a.split;
+        const int nt = (int)(p1 - p0);
+        const int64_t s = st * NT + tid;
+        const Seg32 r = a.s32[s];
+        const float em1 = r.d.w - 1.f;   // Xdot.Xhat
+        const float hv = fmaf(-0.5f, r.k.w, 0.5f);
+        const SegCap sc = a.scaps[st];
+        float ahi[kAcc], alo[kAcc];
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) ahi[k] = alo[k] = 0.f;
+
+        if (tid == 0) {
+            const int pro = nt < kStages ? nt : kStages;
+            for (int i = 0; i < pro; ++i) issue_tile<Pix32, TP>(sbuf, bars, a.p32, p0 + i, gl + i);
+        }
+        int i = 0;
+        for (; i < nt; ++i) {
+            const uint32_t gi = gl + i;
+            const int buf = gi % kStages;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+                s_abort = 1;
+            } else {
+                const int64_t pt = p0 + i;
+                const float4 pc = a.pcaps[pt];
+                const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
+                const float gap = sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w;
+                const float bx = pc.x - sc.b.x, by = pc.y - sc.b.y, bz = pc.z - sc.b.z;
+                const bool fast_b = sc.b.w < 0.f || sqrtf(bx * bx + by * by + bz * bz) > pc.w + sc.b.w;
+                const bool far = fast_b && (gap >= a.d_far);
+                const Pix32 *sp = sbuf + buf * TP;
+                // FP32 partial sums over windows of 32 pixels, folded into compensated (hi, lo) pairs
+                for (int w0 = 0; w0 < TP; w0 += 32) {
+                    float part[kAcc];
+#pragma unroll
+                    for (int k = 0; k < kAcc; ++k) part[k] = 0.f;
+                    if (far) {
+#pragma unroll 2
+                        for (int q = w0; q < w0 + 32; ++q) {
+                            const float4 pa = sp[q].a;
+                            const float h = fmaf(-pa.z, r.a.z, fmaf(-pa.y, r.a.y, fmaf(-pa.x, r.a.x, 1.f)));
+                            const float A = fmaf(pa.z, r.e.z, fmaf(pa.y, r.e.y, pa.x * r.e.x));
+                            const float B = fmaf(pa.z, r.d.z, fmaf(pa.y, r.d.y, fmaf(pa.x, r.d.x, 1.f)));
+                            adj_pair32<NG9>(2.f * h, A, B, B - r.d.w, A - r.e.w, em1, r.e.w, pa.w, pa.x, pa.y, pa.z,
+                                            part);
+                        }
+                    } else {
+                        const float b_tiny = a.b_min * 1e-3f;
+                        for (int q = w0; q < w0 + 32; ++q) {
+                            const float4 pa = sp[q].a, pb = sp[q].b;
+                            const float dx = (pa.x - r.a.x) + (pb.x - r.b.x);
+                            const float dy = (pa.y - r.a.y) + (pb.y - r.b.y);
+                            const float dz = (pa.z - r.a.z) + (pb.z - r.b.z);
+                            const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            const float Pd = fmaf(r.d.z, dz, fmaf(r.d.y, dy, r.d.x * dx));
+                            const float Qd = fmaf(r.e.z, dz, fmaf(r.e.y, dy, r.e.x * dx));
+                            const float A = fmaf(pa.z, r.e.z, fmaf(pa.y, r.e.y, pa.x * r.e.x));
+                            const float wx = pa.x + r.k.x, wy = pa.y + r.k.y, wz = pa.z + r.k.z;
+                            const float B = fmaf(hv, fmaf(wz, wz, fmaf(wy, wy, wx * wx)), r.k.w);
+                            if (Q < r.b.w || B < b_tiny) {
+                                const Pix64 px = a.p64[pt * TP + q];
+                                if (px.g != 0.0) {
+                                    double t64[kAcc];
+#pragma unroll
+                                    for (int k = 0; k < kAcc; ++k) t64[k] = 0.0;
+                                    const Seg64 s64 = a.s64[s];
+                                    adj_pair64(px.n[0], px.n[1], px.n[2], px.g, s64, NG, t64, zerocnt);
+                                    ++nearcnt;
+#pragma unroll
+                                    for (int k = 0; k < kAcc; ++k) {
+                                        const float th = __double2float_rn(t64[k]);
+                                        fold(ahi[k], alo[k], th);
+                                        alo[k] += __double2float_rn(t64[k] - (double)th);
+                                    }
+                                }
+                            } else {
+                                adj_pair32<NG9>(Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < kAcc; ++k) fold(ahi[k], alo[k], part[k]);
+                }
+            }
+            __syncthreads();
+            if (s_abort) break;
+            if (tid == 0 && i + kStages < nt) issue_tile<Pix32, TP>(sbuf, bars, a.p32, p0 + i + kStages, gi + kStages);
+        }
+        if (s_abort) {
+            if (tid == 0) {
+                atomicOr(&a.st->bits, kStatTimeout);
+                drain<TP>(bars, gl, i, nt);
+            }
+            return;
+        }
+        gl += nt;
+        if (s < a.n) {
+            const Seg64 s64 = a.s64[s];
+            double acc[kAcc], out[9];
+#pragma unroll
+            for (int k = 0; k < kAcc; ++k) acc[k] = (double)ahi[k] + (double)alo[k];
+            adj_assemble(s64, acc, NG, out);
+            if (a.split == 1) {
+                for (int k = 0; k < NG; ++k) a.grad[k * a.ld_g + s] = out[k];
+            } else {
+                for (int k = 0; k < NG; ++k) a.partial[((int64_t)kc * NG + k) * a.n_pad + s] = out[k];
+            }
+        }
+    }
+    const int lane = tid & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+        nearcnt += __shfl_xor_sync(0xffffffffu, nearcnt, o);
+        zerocnt += __shfl_xor_sync(0xffffffffu, zerocnt, o);
+    }
+    if (lane == 0 && (nearcnt | zerocnt)) {
+        atomicAdd(&a.st->near_pairs, (unsigned long long)nearcnt);
+        atomicAdd(&a.st->zero_pairs, (unsigned long long)zerocnt);
+    }
+}
+
+template <int NT, int TP>
+__global__ void __launch_bounds__(NT) k_adj_f64(AdjArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    Pix64 *sbuf = reinterpret_cast<Pix64 *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * TP * sizeof(Pix64));
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int NG = a.ngrad;
+    unsigned zerocnt = 0;
+    uint32_t gl = 0;
+    const int64_t n_items = a.nseg_tiles * a.split;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t st = item / a.split;
+        const int kc = (int)(item - st * a.split);
+        const int64_t p0 = a.npix_tiles * kc / a.split, p1 = a.npix_tiles * (kc + 1) / a.split;
+        const int nt = (int)(p1 - p0);
+        const int64_t s = st * NT + tid;
+        const Seg64 s64 = a.s64[s];
+        double acc[kAcc];
+        for (int k = 0; k < kAcc; ++k) acc[k] = 0.0;
+        if (tid == 0) {
+            const int pro = nt < kStages ? nt : kStages;
+            for (int i = 0; i < pro; ++i) issue_tile<Pix64, TP>(sbuf, bars, a.p64, p0 + i, gl + i);
+        }
+        int i = 0;
+        for (; i < nt; ++i) {
+            const uint32_t gi = gl + i;
+            const int buf = gi % kStages;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+                s_abort = 1;
+            } else {
+                const Pix64 *sp = sbuf + buf * TP;
+                double part[kAcc];
+                for (int k = 0; k < kAcc; ++k) part[k] = 0.0;
+                unsigned z = 0;
+                for (int q = 0; q < TP; ++q) {
+                    const Pix64 px = sp[q];
+                    if (px.g != 0.0) adj_pair64(px.n[0], px.n[1], px.n[2], px.g, s64, NG, part, z);
+                }
+                if (s < a.n) zerocnt += z;
+                for (int k = 0; k < kAcc; ++k) acc[k] += part[k];
+            }
+            __syncthreads();
+            if (s_abort) break;
+            if (tid == 0 && i + kStages < nt) issue_tile<Pix64, TP>(sbuf, bars, a.p64, p0 + i + kStages, gi + kStages);
+        }
+        if (s_abort) {
+            if (tid == 0) {
+                atomicOr(&a.st->bits, kStatTimeout);
+                drain<TP>(bars, gl, i, nt);
+            }
+            return;
+        }
+        gl += nt;
+        if (s < a.n) {
+            double out[9];
+            adj_assemble(s64, acc, NG, out);
+            if (a.split == 1) {
+                for (int k = 0; k < NG; ++k) a.grad[k * a.ld_g + s] = out[k];
+            } else {
+                for (int k = 0; k < NG; ++k) a.partial[((int64_t)kc * NG + k) * a.n_pad + s] = out[k];
+            }
+        }
+    }
+    const int lane = tid & 31;
+    for (int o = 16; o > 0; o >>= 1) zerocnt += __shfl_xor_sync(0xffffffffu, zerocnt, o);
+    if (lane == 0 && zerocnt) atomicAdd(&a.st->zero_pairs, (unsigned long long)zerocnt);
+}
+
+// grad[k][s] = sum over chunks c = 0..split-1 of partial[c][k][s], fixed order, compensated
+__global__ void k_adj_reduce(const double *__restrict__ partial, int split, int ngrad, int64_t n, int64_t n_pad,
+                             double *__restrict__ grad, int64_t ld_g)
+{
+    const int64_t tot = (int64_t)ngrad * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx / n, s = idx - k * n;
+        double hi = 0.0, lo = 0.0;
+        for (int c = 0; c < split; ++c) fold64(hi, lo, partial[((int64_t)c * ngrad + k) * n_pad + s]);
+        grad[k * ld_g + s] = hi + lo;
+    }
+}
+
+namespace {
+constexpr int kAdjNT = 128, kAdjTP = 256, kAdj64NT = 128, kAdj64TP = 128;
+size_t smem_adj32() { return kStages * kAdjTP * sizeof(Pix32) + kStages * sizeof(uint64_t); }
+size_t smem_adj64() { return kStages * kAdj64TP * sizeof(Pix64) + kStages * sizeof(uint64_t); }
+}  // namespace
+
+int adj_seg_tile(int prec) { return prec == ISW_F32C ? kAdjNT : kAdj64NT; }
+int adj_pix_tile(int prec) { return prec == ISW_F32C ? kAdjTP : kAdj64TP; }
+
+int adj_slots(int prec, int ngrad, int num_sms)
+{
+    int nb = 0;
+    if (prec == ISW_F32C) {
+        const void *fn = ngrad == 9 ? (const void *)&k_adj_f32c<kAdjNT, kAdjTP, true>
+                                    : (const void *)&k_adj_f32c<kAdjNT, kAdjTP, false>;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kAdjNT, smem_adj32());
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)&k_adj_f64<kAdj64NT, kAdj64TP>, kAdj64NT,
+                                                      smem_adj64());
+    }
+    return (nb > 0 ? nb : 1) * num_sms;
+}
+
+void launch_pack_pixels(const double *nv, int64_t ldn, const int64_t *outidx, const double *g, int64_t tot,
+                        Pix32 *p32, Pix64 *p64, cudaStream_t s)
+{
+    int64_t blocks = (tot + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
+    k_pack_pixels<<<(unsigned)blocks, 256, 0, s>>>(nv, ldn, outidx, g, tot, p32, p64);
+}
+
+void launch_adjoint(int prec, const AdjArgs &a, int grid, cudaStream_t s)
+{
+    void *args[] = {(void *)&a};
+    if (prec == ISW_F32C) {
+        const void *fn = a.ngrad == 9 ? (const void *)&k_adj_f32c<kAdjNT, kAdjTP, true>
+                                      : (const void *)&k_adj_f32c<kAdjNT, kAdjTP, false>;
+        cudaLaunchKernel(fn, dim3(grid), dim3(kAdjNT), args, smem_adj32(), s);
+    } else {
+        cudaLaunchKernel((const void *)&k_adj_f64<kAdj64NT, kAdj64TP>, dim3(grid), dim3(kAdj64NT), args,
+                         smem_adj64(), s);
+    }
+    if (a.split > 1) {
+        const int64_t tot = (int64_t)a.ngrad * a.n;
+        int64_t blocks = (tot + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        k_adj_reduce<<<(unsigned)blocks, 256, 0, s>>>(a.partial, a.split, a.ngrad, a.n, a.n_pad, a.grad, a.ld_g);
+    }
+}
+
+}  // namespace isw

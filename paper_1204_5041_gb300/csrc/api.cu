@@ -12,7 +12,10 @@ using namespace isw;
 
 namespace {
 
-enum WsSlot { kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc, kWsCount };
+enum WsSlot {
+    kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
+    kWsP32, kWsP64, kWsAdjPartial, kWsCount
+};
 
 int set_err(isw_ctx *c, int code, const char *fmt, ...)
 {
@@ -443,9 +446,89 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
                     const double *samples, int64_t n, int64_t ld, const double *x_obs, double GU, int prec,
                     const double *dL_dtheta, double *grad_out, int64_t ld_g, int ngrad, void *stream)
 {
-    (void)nside; (void)pix0; (void)npix; (void)pix_list; (void)samples; (void)n; (void)ld; (void)x_obs;
-    (void)GU; (void)prec; (void)dL_dtheta; (void)grad_out; (void)ld_g; (void)ngrad; (void)stream;
-    return set_err(c, ISW_EINVAL, "isw_map_adjoint: not built yet");
+    if (!c) return ISW_EINVAL;
+    int r;
+    if ((r = check_pixels(c, nside, pix0, npix, pix_list))) return r;
+    if ((r = check_samples(c, samples, n, ld))) return r;
+    if (prec != ISW_F64 && prec != ISW_F32C) return set_err(c, ISW_EINVAL, "unknown precision %d", prec);
+    if (ngrad != 6 && ngrad != 9) return set_err(c, ISW_EINVAL, "ngrad must be 6 or 9");
+    if (n == 0) return ISW_OK;
+    if (ld_g < n) return set_err(c, ISW_EINVAL, "ld_g < n");
+    if (!is_device_ptr(grad_out)) return set_err(c, ISW_EINVAL, "grad_out is not a device pointer");
+    if (npix > 0 && !is_device_ptr(dL_dtheta)) return set_err(c, ISW_EINVAL, "dL_dtheta is not a device pointer");
+    if (!std::isfinite(GU)) return set_err(c, ISW_EINVAL, "GU not finite");
+    if ((r = set_device(c))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (npix == 0) {
+        for (int k = 0; k < ngrad; ++k) {
+            cudaError_t e = cudaMemsetAsync(grad_out + (int64_t)k * ld_g, 0, (size_t)n * sizeof(double), s);
+            if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync");
+        }
+        return ISW_OK;
+    }
+    const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
+    const int NT = adj_seg_tile(prec), TP = adj_pix_tile(prec);
+    const Variant pv{0, 0, 0, 32, TP / 32};
+    const PixelPlan pp = plan_pixels(nside, pix0, npix, pix_list, pv);
+    const int64_t n_pad = (n + NT - 1) / NT * NT;
+    const int64_t nseg_tiles = n_pad / NT;
+    const int slots = adj_slots(prec, ngrad, c->num_sms);
+    int split = c->split_override > 0 ? c->split_override : choose_split(nseg_tiles, pp.ntiles, slots);
+    if (split > pp.ntiles) split = (int)pp.ntiles;
+    if ((r = ensure_ws(c, kWsNv, (size_t)pp.tot * 3 * sizeof(double)))) return r;
+    if ((r = ensure_ws(c, kWsOut, (size_t)pp.tot * sizeof(int64_t)))) return r;
+    if ((r = ensure_ws(c, kWsPcap, (size_t)pp.ntiles * sizeof(float4)))) return r;
+    if ((r = ensure_ws(c, kWsP32, (size_t)pp.tot * sizeof(Pix32)))) return r;
+    if ((r = ensure_ws(c, kWsP64, (size_t)pp.tot * sizeof(Pix64)))) return r;
+    if ((r = ensure_ws(c, kWsS32, (size_t)n_pad * sizeof(Seg32)))) return r;
+    if ((r = ensure_ws(c, kWsS64, (size_t)n_pad * sizeof(Seg64)))) return r;
+    if ((r = ensure_ws(c, kWsScap, (size_t)nseg_tiles * sizeof(SegCap)))) return r;
+    if (split > 1 && (r = ensure_ws(c, kWsAdjPartial, (size_t)split * ngrad * n_pad * sizeof(double)))) return r;
+    const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
+    double *nv = (double *)c->ws[kWsNv];
+    int64_t *outidx = (int64_t *)c->ws[kWsOut];
+    float4 *pcaps = (float4 *)c->ws[kWsPcap];
+    Pix32 *p32 = (Pix32 *)c->ws[kWsP32];
+    Pix64 *p64 = (Pix64 *)c->ws[kWsP64];
+    Seg32 *s32 = (Seg32 *)c->ws[kWsS32];
+    Seg64 *s64 = (Seg64 *)c->ws[kWsS64];
+    SegCap *scaps = (SegCap *)c->ws[kWsScap];
+    launch_pixel_table(nside, pp.mode, pix0, npix, pix_list, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx, pcaps,
+                       c->d_status, s);
+    launch_pack_pixels(nv, pp.tot, outidx, dL_dtheta, pp.tot, p32, p64, s);
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, c->d_status, s);
+    c->n_launch += 4;
+    if (prec == ISW_F32C) {
+        launch_seg_caps(s32, s64, n, n_pad, NT, (float)c->b_min, scaps, s);
+        c->n_launch += 1;
+    }
+    AdjArgs a;
+    a.p32 = p32;
+    a.p64 = p64;
+    a.pcaps = pcaps;
+    a.npix_tiles = pp.ntiles;
+    a.s32 = s32;
+    a.s64 = s64;
+    a.scaps = scaps;
+    a.nseg_tiles = nseg_tiles;
+    a.n = n;
+    a.n_pad = n_pad;
+    a.split = split;
+    a.ngrad = ngrad;
+    a.b_min = (float)c->b_min;
+    a.d_far = (float)c->d_far;
+    a.grad = grad_out;
+    a.ld_g = ld_g;
+    a.partial = split > 1 ? (double *)c->ws[kWsAdjPartial] : nullptr;
+    a.st = c->d_status;
+    const int64_t items = nseg_tiles * split;
+    const int grid = (int)(items < slots ? items : slots);
+    const int ti = timing_begin(c, s);
+    launch_adjoint(prec, a, grid, s);
+    timing_end(c, ti, s);
+    c->n_pair += 1;
+    c->n_launch += split > 1 ? 2 : 1;
+    return check_launch(c, "isw_map_adjoint launch");
 }
 
 int isw_map_batched(isw_ctx *c, int64_t nside, const double *nodes, int64_t ld, const int64_t *shell_off,

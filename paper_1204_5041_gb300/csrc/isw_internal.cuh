@@ -270,7 +270,7 @@ struct DevStatus {
 // radius, e = 1 + Xdot.Xhat, f = X'.Xhat (so that Xdot.d = B - e and X'.d = A - f for
 // d = n - Xhat); the last four give B = (1 - |Xdot|) + |Xdot| |n + Xdot/|Xdot||^2 / 2
 // without cancellation when n approaches -Xdot/|Xdot|.
-// FP64 record (128 B): Xhat hi (3), Xhat lo (3), Xdot (3), X' (3), c, 1 - |Xdot|, 0, 0.
+// FP64 record (128 B): Xhat hi (3), Xhat lo (3), Xdot (3), X' (3), c, 1 - |Xdot|, |X - x_obs|, 0.
 // Segment tile cap (48 B): centre (3), chord radius, max rho, min (1 - |Xdot|), beam cap (4).
 // Pixel tile cap (16 B): centre (3), chord radius.
 // ------------------------------------------------------------------------------------
@@ -278,7 +278,15 @@ struct __align__(16) Seg32 {
     float4 a, b, d, e, k;
 };
 struct __align__(16) Seg64 {
-    double xh[3], xl[3], xd[3], xp[3], c, om, pad0, pad1;
+    double xh[3], xl[3], xd[3], xp[3], c, om, X, pad1;   // X = |X_s - x_obs|
+};
+// Pixel records of the adjoint: FP32 (n hi, g | n lo, 0) and FP64 (n, g); padding slots
+// hold n = 0, g = 0 so that every pair stays finite and contributes nothing.
+struct __align__(16) Pix32 {
+    float4 a, b;
+};
+struct __align__(16) Pix64 {
+    double n[3], g;
 };
 struct __align__(16) SegCap {
     float4 c;   // centre xyz, chord radius
@@ -305,8 +313,8 @@ struct isw_ctx {
     char last_error[512];
     isw::DevStatus *d_status;     // device status word + counters
     // workspace buffers (grown on demand, never shrunk)
-    void *ws[8];
-    size_t ws_size[8];
+    void *ws[16];
+    size_t ws_size[16];
     // tunables
     double near_k;      // near-field radius in units of max(pixel size, segment angle)
     double b_min;       // 1 + n.Xdot below this goes to FP64

@@ -63,4 +63,30 @@ void launch_map_f32c(int idx, const MapArgs &a, int grid, cudaStream_t s);
 void launch_map_f64(const MapArgs &a, int grid, cudaStream_t s);
 void launch_reduce_partials(const MapArgs &a, int tile_sz, cudaStream_t s);
 
+// adjoint.cu
+struct AdjArgs {
+    const Pix32 *p32;        // pixel records in tile order
+    const Pix64 *p64;
+    const float4 *pcaps;     // pixel tile caps
+    int64_t npix_tiles;
+    const Seg32 *s32;
+    const Seg64 *s64;
+    const SegCap *scaps;     // caps of the adjoint's sample tiles
+    int64_t nseg_tiles;
+    int64_t n, n_pad;
+    int split;               // pixel chunks
+    int ngrad;               // 6 or 9
+    float b_min, d_far;
+    double *grad;            // [ngrad][ld_g]
+    int64_t ld_g;
+    double *partial;         // [split][ngrad][n_pad] when split > 1
+    DevStatus *st;
+};
+int adj_seg_tile(int prec);
+int adj_pix_tile(int prec);
+int adj_slots(int prec, int ngrad, int num_sms);
+void launch_pack_pixels(const double *nv, int64_t ldn, const int64_t *outidx, const double *g, int64_t tot,
+                        Pix32 *p32, Pix64 *p64, cudaStream_t s);
+void launch_adjoint(int prec, const AdjArgs &a, int grid, cudaStream_t s);
+
 }  // namespace isw

@@ -1,0 +1,65 @@
+// Device helpers shared by the pair kernels (map.cu, adjoint.cu): the FP64 pair term, the
+// compensated folds, and the shared-memory stage ring fed by 1-D bulk copies.
+#pragma once
+
+#include "isw_internal.cuh"
+
+namespace isw {
+
+constexpr int kStages = 4;
+
+// FP64 pair term (d = (n - Xhat_hi) - Xhat_lo keeps full relative accuracy near the string)
+__device__ __forceinline__ double pair64(double nx, double ny, double nz, const Seg64 &g, unsigned &zero)
+{
+    const double dx = (nx - g.xh[0]) - g.xl[0];
+    const double dy = (ny - g.xh[1]) - g.xl[1];
+    const double dz = (nz - g.xh[2]) - g.xl[2];
+    const double Q = dx * dx + dy * dy + dz * dz;
+    if (Q == 0.0) {
+        ++zero;
+        return 0.0;
+    }
+    const double A = nx * g.xp[0] + ny * g.xp[1] + nz * g.xp[2];
+    const double B = 1.0 + (nx * g.xd[0] + ny * g.xd[1] + nz * g.xd[2]);
+    const double Pd = g.xd[0] * dx + g.xd[1] * dy + g.xd[2] * dz;
+    const double Qd = g.xp[0] * dx + g.xp[1] * dy + g.xp[2] * dz;
+    return g.c * (B * Pd - A * Qd) / (B * Q);
+}
+
+__device__ __forceinline__ void fold(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
+__device__ __forceinline__ void fold64(double &hi, double &lo, double x)
+{
+    const double s = hi + x;
+    const double bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
+// Issue the bulk copy of segment tile j into stage (load index gi) -- one thread.
+template <typename Rec, int S>
+__device__ __forceinline__ void issue_tile(Rec *sbuf, uint64_t *bars, const Rec *src, int64_t j, uint32_t gi)
+{
+    const int b = gi % kStages;
+    mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Rec)));
+    bulk_g2s(sbuf + b * S, src + j * S, (uint32_t)(S * sizeof(Rec)), &bars[b]);
+}
+
+// After a timeout: wait (bounded) for every copy still in flight before leaving the CTA.
+template <int S>
+__device__ __forceinline__ void drain(uint64_t *bars, uint32_t g, int i, int nt)
+{
+    const int last = (i + kStages < nt) ? i + kStages : nt;
+    for (int m = i; m < last; ++m) {
+        const uint32_t gm = g + m;
+        (void)mbar_wait_bounded(&bars[gm % kStages], (gm / kStages) & 1);
+    }
+}
+
+}  // namespace isw
