@@ -14,7 +14,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsCount
 };
 
 int set_err(isw_ctx *c, int code, const char *fmt, ...)
@@ -47,10 +47,21 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+void drop_graph(isw_ctx *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_key = 0;
+}
+
 int ensure_ws(isw_ctx *c, int slot, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (c->ws_size[slot] >= bytes) return ISW_OK;
+    if (c->capturing) return set_err(c, ISW_ECUDA, "workspace growth during graph capture");
+    drop_graph(c);  // a captured graph refers to the old buffers
     if (c->ws[slot]) {
         cudaError_t e = cudaFree(c->ws[slot]);
         c->ws[slot] = nullptr;
@@ -148,7 +159,7 @@ int choose_split(int64_t ntiles, int64_t nst, int slots)
 // Events around a pair-kernel launch when timing is on; returns the slot or -1.
 int timing_begin(isw_ctx *c, cudaStream_t s)
 {
-    if (!c->timing || c->n_timed >= kMaxTimed) return -1;
+    if (!c->timing || c->capturing || c->n_timed >= kMaxTimed) return -1;
     if (!c->ev) {
         c->ev = (cudaEvent_t *)calloc(2 * kMaxTimed, sizeof(cudaEvent_t));
         if (!c->ev) return -1;
@@ -183,7 +194,8 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     }
     int vidx = 0;
     if (prec == ISW_F32C) {
-        vidx = c->tile_override >= 0 && c->tile_override < num_f32_variants() ? c->tile_override : 0;
+        if (c->tile_override >= 0 && c->tile_override < num_f32_variants()) vidx = c->tile_override;
+        else if (c->tuned_nside == nside && c->tuned_n == n) vidx = c->auto_variant;
     }
     const Variant v = prec == ISW_F32C ? f32_variant(vidx) : f64_variant();
     const int S = v.seg_tile;
@@ -271,6 +283,8 @@ int isw_create(isw_ctx **out, int device)
     c->d_far = 0.4;
     c->split_override = 0;
     c->tile_override = -1;
+    c->tuned_nside = -1;
+    c->meta_nshell = -1;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(DevStatus));
@@ -297,6 +311,9 @@ int isw_destroy(isw_ctx *c)
             if (c->ev[e]) cudaEventDestroy(c->ev[e]);
         free(c->ev);
     }
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->d_status) cudaFree(c->d_status);
     free(c);
     return ISW_OK;
@@ -536,10 +553,168 @@ int isw_map_batched(isw_ctx *c, int64_t nside, const double *nodes, int64_t ld, 
                     int64_t nloops, int64_t ldp, const double *x_obs, double t_obs, double GU, int prec, int flags,
                     int accumulate, double *theta_out, void *stream)
 {
-    (void)nside; (void)nodes; (void)ld; (void)shell_off; (void)nshell; (void)t_box; (void)mode;
-    (void)loop_params; (void)nloops; (void)ldp; (void)x_obs; (void)t_obs; (void)GU; (void)prec; (void)flags;
-    (void)accumulate; (void)theta_out; (void)stream;
-    return set_err(c, ISW_EINVAL, "isw_map_batched: not built yet");
+    if (!c) return ISW_EINVAL;
+    if (nside < 1 || nside > (1 << 24)) return set_err(c, ISW_EINVAL, "nside out of range");
+    if (nshell < 0 || (nshell > 0 && (!shell_off || !t_box || !mode)))
+        return set_err(c, ISW_EINVAL, "shell_off, t_box and mode (host arrays) are required");
+    if (prec != ISW_F64 && prec != ISW_F32C) return set_err(c, ISW_EINVAL, "unknown precision %d", prec);
+    if (flags & ~(ISW_SKIP_LIGHTCONE | ISW_GRAPH | ISW_AUTOTUNE)) return set_err(c, ISW_EINVAL, "unknown flags");
+    const int64_t n = nshell > 0 ? shell_off[nshell] : 0;
+    if (nshell > 0 && shell_off[0] != 0) return set_err(c, ISW_EINVAL, "shell_off[0] must be 0");
+    bool has_burden = false;
+    for (int64_t k = 0; k < nshell; ++k) {
+        if (shell_off[k + 1] < shell_off[k]) return set_err(c, ISW_EINVAL, "shell_off must be non-decreasing");
+        if (mode[k] != ISW_LINEAR && mode[k] != ISW_BURDEN) return set_err(c, ISW_EINVAL, "bad mode in shell %lld", (long long)k);
+        if (mode[k] == ISW_LINEAR && !(t_obs > t_box[k])) return set_err(c, ISW_EINVAL, "t_obs must exceed t_box");
+        if (mode[k] == ISW_BURDEN) has_burden = true;
+    }
+    int r;
+    if ((r = check_samples(c, nodes, n, ld))) return r;
+    if (!is_device_ptr(theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
+    if (has_burden && !(flags & ISW_SKIP_LIGHTCONE) && (nloops <= 0 || ldp < nloops || !is_device_ptr(loop_params)))
+        return set_err(c, ISW_EINVAL, "BURDEN shells need device loop_params[17][ldp], ldp >= nloops > 0");
+    if (!std::isfinite(t_obs) || !std::isfinite(GU)) return set_err(c, ISW_EINVAL, "t_obs / GU not finite");
+    if ((r = set_device(c))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t npix = 12 * nside * nside;
+    const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
+
+    // shell metadata on the device (uploaded when it changes)
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](const void *p, size_t bytes) {
+        const unsigned char *b = (const unsigned char *)p;
+        for (size_t k = 0; k < bytes; ++k) h = (h ^ b[k]) * 1099511628211ull;
+    };
+    mix(shell_off, (size_t)(nshell + 1) * sizeof(int64_t));
+    mix(t_box, (size_t)nshell * sizeof(double));
+    mix(mode, (size_t)nshell * sizeof(int32_t));
+    const size_t meta_bytes = (size_t)(nshell + 1) * 8 + (size_t)nshell * 8 + (size_t)nshell * 4 + 64;
+    if ((r = ensure_ws(c, kWsShell, meta_bytes))) return r;
+    int64_t *d_off = (int64_t *)c->ws[kWsShell];
+    double *d_tbox = (double *)(d_off + nshell + 1);
+    int32_t *d_mode = (int32_t *)(d_tbox + nshell);
+    if (h != c->meta_hash || nshell != c->meta_nshell) {
+        // earlier batched work on this stream may still read the previous metadata
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaMemcpy(d_off, shell_off, (size_t)(nshell + 1) * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_tbox, t_box, (size_t)nshell * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_mode, mode, (size_t)nshell * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_err(c, e, "shell metadata upload");
+        c->meta_hash = h;
+        c->meta_nshell = nshell;
+    }
+    const bool skip_lc = (flags & ISW_SKIP_LIGHTCONE) != 0;
+    if (!skip_lc && (r = ensure_ws(c, kWsSamples, (size_t)(n > 0 ? n : 1) * 10 * sizeof(double)))) return r;
+    const double *samples = skip_lc ? nodes : (const double *)c->ws[kWsSamples];
+    const int64_t lds = skip_lc ? ld : n;
+    const double tol = 4.0 * (std::nextafter(t_obs, INFINITY) - t_obs);
+
+    auto enqueue = [&](cudaStream_t st) -> int {
+        if (!skip_lc && n > 0) {
+            launch_lightcone_shells(nodes, n, ld, d_off, nshell, d_tbox, d_mode, loop_params, nloops, ldp, xo[0],
+                                    xo[1], xo[2], t_obs, tol, (double *)c->ws[kWsSamples], n, c->d_status, st);
+            c->n_launch += 1;
+        }
+        return map_impl(c, nside, 0, npix, nullptr, samples, n, lds, x_obs, GU, prec, accumulate, theta_out, st);
+    };
+
+    // autotuner: time every FP32 variant on a prefix of the samples, keep the fastest
+    if ((flags & ISW_AUTOTUNE) && prec == ISW_F32C && n > 0 && c->tile_override < 0 &&
+        !(c->tuned_nside == nside && c->tuned_n == n)) {
+        if (!skip_lc) {
+            launch_lightcone_shells(nodes, n, ld, d_off, nshell, d_tbox, d_mode, loop_params, nloops, ldp, xo[0],
+                                    xo[1], xo[2], t_obs, tol, (double *)c->ws[kWsSamples], n, c->d_status, s);
+            c->n_launch += 1;
+        }
+        const int64_t nt = n < 16384 ? n : 16384;   // prefix of the samples used for timing
+        if ((r = ensure_ws(c, kWsMisc, (size_t)npix * sizeof(double)))) return r;
+        double *scratch_theta = (double *)c->ws[kWsMisc];
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_v = 0;
+        const int saved_timing = c->timing;
+        c->timing = 0;
+        for (int v = 0; v < num_f32_variants(); ++v) {
+            c->tile_override = v;
+            float tv = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, s);
+                r = map_impl(c, nside, 0, npix, nullptr, samples, nt, lds, x_obs, GU, prec, 0, scratch_theta, s);
+                cudaEventRecord(e1, s);
+                if (r) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1) tv = ms;
+            }
+            if (r) break;
+            if (tv < best) {
+                best = tv;
+                best_v = v;
+            }
+        }
+        c->tile_override = -1;
+        c->timing = saved_timing;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (r) return r;
+        c->auto_variant = best_v;
+        c->tuned_nside = nside;
+        c->tuned_n = n;
+    }
+
+    if (!(flags & ISW_GRAPH)) return enqueue(s);
+
+    // CUDA graph: capture the light cone + map once per argument set, replay afterwards
+    uint64_t key = h;
+    auto mixv = [&key](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+    mixv((uint64_t)nside); mixv((uint64_t)(uintptr_t)nodes); mixv((uint64_t)ld); mixv((uint64_t)nshell);
+    mixv((uint64_t)(uintptr_t)loop_params); mixv((uint64_t)nloops); mixv((uint64_t)ldp);
+    double dv[8] = {xo[0], xo[1], xo[2], t_obs, GU, c->near_k, c->b_min, c->d_far};
+    for (double d : dv) { uint64_t u; memcpy(&u, &d, 8); mixv(u); }
+    mixv((uint64_t)prec); mixv((uint64_t)flags); mixv((uint64_t)accumulate); mixv((uint64_t)(uintptr_t)theta_out);
+    mixv((uint64_t)c->split_override); mixv((uint64_t)(c->tile_override + 1)); mixv((uint64_t)c->auto_variant);
+    if (c->graph_exec && key == c->graph_key) {
+        cudaError_t e = cudaGraphLaunch(c->graph_exec, s);
+        if (e != cudaSuccess) return cuda_err(c, e, "cudaGraphLaunch");
+        c->n_launch += c->graph_kernels;
+        c->n_pair += c->graph_pairs;
+        return ISW_OK;
+    }
+    // first call with these arguments: run eagerly (this also sizes the workspace), then capture
+    if ((r = enqueue(s))) return r;
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamCreate");
+    }
+    drop_graph(c);
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamBeginCapture");
+    c->capturing = 1;
+    const int64_t launches = c->n_launch, pairs = c->n_pair;
+    r = enqueue(c->cap_stream);
+    c->capturing = 0;
+    c->graph_kernels = c->n_launch - launches;
+    c->graph_pairs = c->n_pair - pairs;
+    c->n_launch = launches;
+    c->n_pair = pairs;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_err(c, e, "cudaGraphInstantiate");
+    }
+    c->graph = g;
+    c->graph_key = key;
+    return ISW_OK;
 }
 
 }  // extern "C"

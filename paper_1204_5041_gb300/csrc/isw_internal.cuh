@@ -328,5 +328,17 @@ struct isw_ctx {
     int64_t n_pair;     // pair-kernel launches since the last reset
     int64_t n_launch;   // all kernel launches since the last reset
     cudaEvent_t *ev;    // 2 * kMaxTimed events, created on first use
+    // FP32 variant picked by the autotuner for (tuned_nside, tuned_n); used when no override
+    int auto_variant;
+    int64_t tuned_nside, tuned_n;
+    // batched path: shell metadata last uploaded, and one captured graph
+    uint64_t meta_hash;
+    int64_t meta_nshell;
+    int capturing;
+    cudaStream_t cap_stream;
+    uint64_t graph_key;
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    int64_t graph_kernels, graph_pairs;  // kernel / pair-kernel launches inside the captured graph
 };
 constexpr int kMaxTimed = 4096;
