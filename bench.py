@@ -4,9 +4,12 @@ Workload (default): Nside=512 RING sky (3,145,728 pixels) and one box of 200,000
 samples -- 234 Burden loops x 512 nodes (BURDEN light-cone solve) plus 8 random-walk long
 strings of 10,024 nodes at box time 0.6 (LINEAR solve) -- seeded synthetic inputs.
 
-One step = the whole hot path on that input: light-cone solve of every node, pixel table
-(RING pix2vec), sample records, the all-pairs map in the FP32-compensated precision (FP64
-near field), written as a float64 RING map.  Inputs are resident in HBM before the timed
+One step = the whole hot path on that input, one isw_map_batched call: light-cone solve of
+every node, pixel table (RING pix2vec), sample records, the all-pairs map in the FP32-
+compensated precision (FP64 near field; kernel variant picked by the library's autotuner in
+the warm-up), written as a float64 RING map.  Also reported, outside the timed region: one
+step of the plain FP64 path, the batched workload (Nside=1024, 64 shells, graph replay) and
+the adjoint workload (Nside=256, 50,176 samples).  Inputs are resident in HBM before the timed
 region; L2 (129 MB) is flushed between steps by writing a 256 MiB buffer outside the timed
 events.  `e2e` repeats the step through the public Python API with the nodes copied from
 pinned host memory and the map copied back every step.
@@ -148,17 +151,15 @@ def run_gpu(args):
     loops_h = torch.from_numpy(np.ascontiguousarray(w.loop_params)).pin_memory()
     loops_d = loops_h.to(dev)
     nodes_d = nodes_h.to(dev)
-    samples_d = torch.empty_like(nodes_d)
     theta_d = torch.empty(w.npix, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    flags = isw.AUTOTUNE if args.variant < 0 else 0
 
-    def step(nodes, samples, theta, prec="f32c"):
-        for k in range(w.nshell):
-            a, b = int(w.shell_off[k]), int(w.shell_off[k + 1])
-            isw.lightcone_intersect(int(w.mode[k]), nodes[:, a:b], loops_d, float(w.t_box[k]), w.x_obs, w.t_obs,
-                                    out=samples[:, a:b])
-        isw.isw_map(w.nside, samples, x_obs=w.x_obs, GU=w.GU, prec=prec, out=theta)
+    def step(nodes, loops, theta, prec="f32c", fl=flags):
+        # light-cone solve of every shell + pixel table + records + pair kernel (+ chunk reduce)
+        isw.isw_map_batched(w.nside, nodes, w.shell_off, w.t_box, w.mode, loops, x_obs=w.x_obs, t_obs=w.t_obs,
+                            GU=w.GU, prec=prec, flags=fl, out=theta)
 
     def barrier():
         torch.cuda.synchronize()
@@ -167,7 +168,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step(nodes_d, samples_d, theta_d)
+        step(nodes_d, loops_d, theta_d)
     r, counts = ctx.check_status()
     if r != isw.OK:
         raise RuntimeError(f"device status {r} during warm-up: {ctx.last_error()}")
@@ -182,7 +183,7 @@ def run_gpu(args):
         for e0, e1 in evs:
             flush.fill_(1.0)
             e0.record(stream)
-            step(nodes_d, samples_d, theta_d)
+            step(nodes_d, loops_d, theta_d)
             e1.record(stream)
         barrier()
     t_wall = time.perf_counter() - t_wall
@@ -200,7 +201,7 @@ def run_gpu(args):
     pairs_step = w.npix * w.n
     value = ws * pairs_step * args.steps / (total_ms / 1e3)
 
-    # ---- end to end through the public API: pinned host nodes in, map out, every step
+    # ---- end to end through the public API: pinned host inputs in, map out, every step
     theta_h = torch.empty(w.npix, dtype=torch.float64).pin_memory()
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -208,32 +209,72 @@ def run_gpu(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         nd = nodes_h.to(dev, non_blocking=True)
-        loops_d.copy_(loops_h, non_blocking=True)
-        step(nd, samples_d, theta_d)
+        ld = loops_h.to(dev, non_blocking=True)
+        step(nd, ld, theta_d)
         theta_h.copy_(theta_d, non_blocking=True)
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     e2e_value = ws * pairs_step / (e2e_ms / 1e3)
 
+    def timed(fn):
+        barrier()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        barrier()
+        return a0.elapsed_time(a1)
+
     # ---- plain FP64 GPU path, one step (outside the timed region), for the FP32/FP64 ratio
     fp64 = None
+    theta64 = None
     if not args.skip_fp64:
         theta64 = torch.empty_like(theta_d)
-        barrier()
-        e0.record(stream)
-        step(nodes_d, samples_d, theta64, prec="f64")
-        e1.record(stream)
-        barrier()
-        ms64 = e0.elapsed_time(e1)
+        ms64 = timed(lambda: step(nodes_d, loops_d, theta64, prec="f64", fl=0))
         fp64 = {"value": pairs_step / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64}
+
+    extra = {}
+    if not args.skip_extra and rank == 0:
+        # batched workload: Nside=1024, 64 cube shells, graph-captured + autotuned
+        w2 = synth.config(2, seed=args.seed)
+        n2 = torch.from_numpy(np.ascontiguousarray(w2.nodes)).to(dev)
+        l2 = torch.from_numpy(np.ascontiguousarray(w2.loop_params)).to(dev)
+        th2 = torch.empty(w2.npix, dtype=torch.float64, device=dev)
+        run2 = lambda: isw.isw_map_batched(w2.nside, n2, w2.shell_off, w2.t_box, w2.mode, l2, prec="f32c",
+                                           flags=isw.GRAPH | isw.AUTOTUNE, out=th2)
+        run2()                                      # autotune + eager run + capture
+        ms2 = timed(run2)                           # graph replay
+        extra["batched"] = {"workload": f"{w2.name}: Nside={w2.nside}, {w2.nshell} light-cone groups "
+                                        f"(64 cube shells), {w2.n:,} samples; one CUDA-graph replay",
+                            "value": w2.npix * w2.n / (ms2 / 1e3), "unit": UNIT, "ms": ms2}
+        del n2, th2
+        # adjoint workload: Nside=256, 98 loops x 512 samples, loss sum (Theta - Theta_t)^2
+        w3 = synth.config(3, seed=args.seed)
+        n3 = torch.from_numpy(np.ascontiguousarray(w3.nodes)).to(dev)
+        l3 = torch.from_numpy(np.ascontiguousarray(w3.loop_params)).to(dev)
+        s3 = isw.lightcone_intersect(isw.BURDEN, n3, l3)
+        th3 = isw.isw_map(w3.nside, s3, prec="f32c")
+        tgt = torch.randn(w3.npix, dtype=torch.float64, device=dev,
+                          generator=torch.Generator(device=dev).manual_seed(args.seed + 1)) * th3.std()
+        g3 = 2 * (th3 - tgt)
+        gout = torch.empty((6, w3.n), dtype=torch.float64, device=dev)
+        isw.isw_map_adjoint(w3.nside, s3, g3, prec="f32c", out=gout)
+        ms3 = timed(lambda: isw.isw_map_adjoint(w3.nside, s3, g3, prec="f32c", out=gout))
+        ms3_64 = timed(lambda: isw.isw_map_adjoint(w3.nside, s3, g3, prec="f64", out=gout))
+        extra["adjoint"] = {"workload": f"{w3.name}: Nside={w3.nside}, {w3.n:,} samples, dL/dX and dL/dXdot",
+                            "value": w3.npix * w3.n / (ms3 / 1e3), "unit": UNIT, "ms": ms3,
+                            "fp64_value": w3.npix * w3.n / (ms3_64 / 1e3), "fp64_ms": ms3_64}
+        r, _ = ctx.check_status()
+        if r != isw.OK:
+            raise RuntimeError(f"device status {r} in the extra measurements: {ctx.last_error()}")
 
     peak, mhz = fp32_peak_tflops()
     map_avg_ms = map_ms / max(map_launches, 1)
     achieved = FLOPS_PER_PAIR * pairs_step / (map_avg_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "isw::k_map_f32c<256,4,64>", "flops_per_pair": FLOPS_PER_PAIR,
-            "kernel_ms": map_avg_ms,
+            "traffic": None, "kernel": "isw::k_map_f32c (pair kernel, autotuned variant)",
+            "flops_per_pair": FLOPS_PER_PAIR, "kernel_ms": map_avg_ms, "kernel_launches": map_launches,
             "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz (max SM clock)"}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -247,8 +288,9 @@ def run_gpu(args):
         "counts_per_step": {k: v / args.steps for k, v in counts.items()},
         "wall_s_timed_region": t_wall,
     }
+    out.update(extra)
     if rank == 0 and not args.skip_cpu:
-        out["cpu_baseline"] = cpu_baseline(w, theta_d, theta64 if fp64 else None, args)
+        out["cpu_baseline"] = cpu_baseline(w, theta_d, theta64, args)
     if ws > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -274,7 +316,7 @@ def cpu_baseline(w, theta32_d, theta64_d, args):
     import oracle
 
     samples, _, _ = oracle.lightcone_workload(w)
-    probe = 64
+    probe = 1024
     _, _, dt, _ = _oracle_sample(w, samples, probe, seed=1)
     npix_sample = int(min(w.npix, max(probe, probe * args.cpu_seconds / max(dt, 1e-3))))
     pix, ref, dt, threads = _oracle_sample(w, samples, npix_sample)
@@ -333,6 +375,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true", help="skip the batched and adjoint sub-measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--variant", type=int, default=-1, help="FP32 pair-kernel variant (-1 = automatic)")
