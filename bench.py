@@ -273,7 +273,7 @@ def run_gpu(args):
     map_avg_ms = map_ms / max(map_launches, 1)
     achieved = FLOPS_PER_PAIR * pairs_step / (map_avg_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "isw::k_map_f32c (pair kernel, autotuned variant)",
+            "traffic": None, "kernel": "pair kernels: isw::k_map_f32c (far field) + k_map_f32c_near, autotuned variant",
             "flops_per_pair": FLOPS_PER_PAIR, "kernel_ms": map_avg_ms, "kernel_launches": map_launches,
             "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz (max SM clock)"}
     out = {
@@ -380,7 +380,7 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=6.0)
     ap.add_argument("--variant", type=int, default=-1, help="FP32 pair-kernel variant (-1 = automatic)")
     ap.add_argument("--split", type=int, default=0, help="segment chunks (0 = automatic)")
-    ap.add_argument("--d-far", type=float, default=None, help="far-field chord threshold (library default 0.4)")
+    ap.add_argument("--d-far", type=float, default=None, help="far-field chord threshold (library default 0.25)")
     ap.add_argument("--b-min", type=float, default=None, help="FP64 routing threshold on 1 + n.Xdot (default 0.01)")
     ap.add_argument("--near-k", type=float, default=None, help="near-field radius factor (default 4)")
     ap.add_argument("--nside", type=int, default=None,

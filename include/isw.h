@@ -91,12 +91,14 @@ int isw_check_status(isw_ctx *ctx, void *stream, int64_t *counts);
  * below near_k * max(pixel size, angular length of the sample's segment); ISW_PARAM_B_MIN
  * (default 0.01): a pair with 1 + n.Xdot below b_min is evaluated in FP64 by the FP32 path;
  * ISW_PARAM_SPLIT: number of segment chunks of the forward maps (0 = automatic);
- * ISW_PARAM_VARIANT: FP32 kernel variant (-1 = automatic); ISW_PARAM_D_FAR (default 0.4):
+ * ISW_PARAM_VARIANT: FP32 kernel variant (-1 = automatic); ISW_PARAM_D_FAR (default 0.25):
  * segment tiles whose every pair is at least this chord apart from the pixel tile use the
  * FP32 far-field form (d.d = 2 (1 - n.Xhat), Xdot.d and X'.d from per-sample constants);
  * 4 disables it; ISW_PARAM_TIMING (default 0):
  * when 1, every launch of the pair kernel (the all-pairs sum of isw_map and
- * isw_map_batched) is bracketed by CUDA events on its stream, read by isw_get_timing. */
+ * isw_map_batched: the FP32 far- and near-field passes and the chunk reduction between them, or
+ * the FP64 kernel and its reduction) is bracketed by CUDA events on its stream, read by
+ * isw_get_timing. */
 int isw_set_param(isw_ctx *ctx, int key, double value);
 
 /* Timing of the pair kernel (ISW_PARAM_TIMING = 1): synchronises the recorded events and
@@ -182,7 +184,7 @@ int isw_map_batched(isw_ctx *ctx, int64_t nside, const double *nodes, int64_t ld
  *   - Needs no isw_ctx and calls no cudaMalloc, cudaFree or allocating library routine.
  *     Its scratch is a static device array of 64 MiB that every GPU loading the library
  *     holds until the process exits; a problem whose scratch does not fit (roughly
- *     40 bytes per padded pixel + 200 bytes per padded sample, e.g. a full Nside=256 sky
+ *     40 bytes per padded pixel + 270 bytes per padded sample, e.g. a full Nside=256 sky
  *     with 10^5 samples) is rejected with ISW_EINVAL before anything is enqueued.
  *   - The first call on a device, with that device current, looks up the array's device
  *     address (cudaGetSymbolAddress); make that first call before any stream capture.

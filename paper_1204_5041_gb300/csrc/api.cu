@@ -14,7 +14,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsCount
 };
 
 int set_err(isw_ctx *c, int code, const char *fmt, ...)
@@ -211,6 +211,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     if ((r = ensure_ws(c, kWsS32, (size_t)n_pad * sizeof(Seg32)))) return r;
     if ((r = ensure_ws(c, kWsS64, (size_t)n_pad * sizeof(Seg64)))) return r;
     if ((r = ensure_ws(c, kWsScap, (size_t)nst * sizeof(SegCap)))) return r;
+    if (prec == ISW_F32C && (r = ensure_ws(c, kWsFar, (size_t)n_pad * sizeof(Far32)))) return r;
     if (split > 1 && (r = ensure_ws(c, kWsPartial, (size_t)split * pp.tot * sizeof(double)))) return r;
 
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
@@ -223,7 +224,8 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
 
     launch_pixel_table(nside, pp.mode, pix0, npix, pix_list, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx, pcaps,
                        c->d_status, s);
-    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, c->d_status, s);
+    Far32 *far = prec == ISW_F32C ? (Far32 *)c->ws[kWsFar] : nullptr;
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, far, c->d_status, s);
     c->n_launch += 3;
     if (prec == ISW_F32C) {
         launch_seg_caps(s32, s64, n, n_pad, S, (float)c->b_min, scaps, s);
@@ -238,6 +240,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.ntiles = pp.ntiles;
     a.s32 = s32;
     a.s64 = s64;
+    a.far = far;
     a.scaps = scaps;
     a.nst = nst;
     a.split = split;
@@ -249,16 +252,23 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.st = c->d_status;
     const int64_t items = pp.ntiles * split;
     const int grid = (int)(items < slots ? items : slots);
+    // the timed pair work: far pass (or the FP64 kernel), chunk reduce, near-field pass
     const int ti = timing_begin(c, s);
-    if (prec == ISW_F32C) launch_map_f32c(vidx, a, grid, s);
-    else launch_map_f64(a, grid, s);
-    timing_end(c, ti, s);
+    if (prec == ISW_F32C) {
+        launch_map_f32c(vidx, a, grid, s);
+        // near-field pass: adds the segment tiles the far pass skipped, chunk by chunk
+        launch_map_f32c_near(vidx, a, c->num_sms, s);
+        c->n_launch += 2;
+    } else {
+        launch_map_f64(a, grid, s);
+        c->n_launch += 1;
+    }
     c->n_pair += 1;
-    c->n_launch += 1;
     if (split > 1) {
         launch_reduce_partials(a, v.tx * v.ty, s);
         c->n_launch += 1;
     }
+    timing_end(c, ti, s);
     return check_launch(c, "isw_map launch");
 }
 
@@ -280,7 +290,7 @@ int isw_create(isw_ctx **out, int device)
     c->device = device;
     c->near_k = 4.0;
     c->b_min = 0.01;
-    c->d_far = 0.4;
+    c->d_far = 0.25;
     c->split_override = 0;
     c->tile_override = -1;
     c->tuned_nside = -1;
@@ -513,7 +523,8 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     launch_pixel_table(nside, pp.mode, pix0, npix, pix_list, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx, pcaps,
                        c->d_status, s);
     launch_pack_pixels(nv, pp.tot, outidx, dL_dtheta, pp.tot, p32, p64, s);
-    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, c->d_status, s);
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, nullptr, c->d_status,
+                s);
     c->n_launch += 4;
     if (prec == ISW_F32C) {
         launch_seg_caps(s32, s64, n, n_pad, NT, (float)c->b_min, scaps, s);

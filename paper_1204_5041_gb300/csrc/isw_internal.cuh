@@ -277,6 +277,14 @@ struct DevStatus {
 struct __align__(16) Seg32 {
     float4 a, b, d, e, k;
 };
+// Far-field record (64 B) with sigma = sign(c), s = sqrt(|c|/2):
+//   a = (-sigma Xhat, sigma), b = (Xdot, -s e/2), c = (s X', -s f/2), d = (s, K, 0, 0),
+//   K = (|c|/2) (f^2 - e^2)/4, so that for |d| >= d_far the pair term is
+//   t = [(s B - s e/2)^2 - (s A - s f/2)^2 + K] / [B sigma (1 - n.Xhat)]   (completed squares of
+//   c/2 [B (B - e) - A (A - f)] / [B (1 - n.Xhat)]).
+struct __align__(16) Far32 {
+    float4 a, b, c, d;
+};
 struct __align__(16) Seg64 {
     double xh[3], xl[3], xd[3], xp[3], c, om, X, pad1;   // X = |X_s - x_obs|
 };

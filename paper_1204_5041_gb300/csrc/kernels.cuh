@@ -24,8 +24,9 @@ void launch_lightcone_shells(const double *nodes, int64_t n, int64_t ld, const i
                              int64_t ld_out, DevStatus *st, cudaStream_t s);
 
 // pack.cu: per-sample records of the map kernels and per-tile caps
+// far (may be NULL): far-field records for the FP32 pair kernel
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
-                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, DevStatus *st,
+                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, Far32 *far, DevStatus *st,
                  cudaStream_t s);
 void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
                      SegCap *caps, cudaStream_t s);
@@ -39,6 +40,7 @@ struct MapArgs {
     int64_t ntiles;          // pixel tiles
     const Seg32 *s32;
     const Seg64 *s64;
+    const Far32 *far;        // far-field records (FP32 kernel)
     const SegCap *scaps;
     int64_t nst;             // segment tiles
     int split;               // segment chunks
@@ -60,6 +62,7 @@ Variant f64_variant();
 int map_f32c_slots(int idx, int num_sms);
 int map_f64_slots(int num_sms);
 void launch_map_f32c(int idx, const MapArgs &a, int grid, cudaStream_t s);
+void launch_map_f32c_near(int idx, const MapArgs &a, int num_sms, cudaStream_t s);
 void launch_map_f64(const MapArgs &a, int grid, cudaStream_t s);
 void launch_reduce_partials(const MapArgs &a, int tile_sz, cudaStream_t s);
 

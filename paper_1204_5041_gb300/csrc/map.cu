@@ -19,14 +19,32 @@
 
 namespace isw {
 
-template <int NT, int P, int S>
-__global__ void __launch_bounds__(NT, (P >= 8 ? 1 : (NT >= 256 ? 2 : 4))) k_map_f32c(MapArgs a)
+// Tile classes of the FP32 kernel: far-field form, mid-range float-pair form, checked loop.
+enum : int { kFar = 0, kMid = 1, kChecked = 2 };
+
+__device__ __forceinline__ int classify(const float4 &pc, const SegCap &sc, float d_far)
+{
+    const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
+    const float gap = sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w;  // lower bound of |d| over the tile pair
+    // B = 1 + n.Xdot >= b_min for every pair unless the pixel cap meets the tile's beam cap
+    const float bx = pc.x - sc.b.x, by = pc.y - sc.b.y, bz = pc.z - sc.b.z;
+    const bool fast_b = sc.b.w < 0.f || sqrtf(bx * bx + by * by + bz * bz) > pc.w + sc.b.w;
+    if (!fast_b || gap < sc.r.x) return kChecked;
+    return gap >= d_far ? kFar : kMid;
+}
+
+// Far-field pass: every segment tile whose class is kFar, in the completed-square form
+// (Far32 records, 14 FP32 ops + 1 rcp per pair); other tiles are skipped here and summed by
+// the near-field pass.  A skipped stage still completes its mbarrier phase (zero-byte arrive).
+template <int NT, int P, int S, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
 {
     constexpr int TILE = NT * P;
     extern __shared__ __align__(128) unsigned char smem[];
-    Seg32 *sbuf = reinterpret_cast<Seg32 *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * S * sizeof(Seg32));
+    Far32 *sbuf = reinterpret_cast<Far32 *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * S * sizeof(Far32));
     __shared__ int s_abort;
+    __shared__ int s_cls[kStages];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
@@ -35,7 +53,6 @@ __global__ void __launch_bounds__(NT, (P >= 8 ? 1 : (NT >= 256 ? 2 : 4))) k_map_
     }
     __syncthreads();
 
-    unsigned nearcnt = 0, zerocnt = 0;
     uint32_t g = 0;
     const int64_t n_items = a.ntiles * a.split;
     const int64_t tot = a.ntiles * TILE;
@@ -45,9 +62,120 @@ __global__ void __launch_bounds__(NT, (P >= 8 ? 1 : (NT >= 256 ? 2 : 4))) k_map_
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
         const int nt = (int)(j1 - j0);
 
+        float nh[P][3], ahi[P], alo[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
+            nh[q][0] = __double2float_rn(a.nv[k]);
+            nh[q][1] = __double2float_rn(a.nv[a.ldn + k]);
+            nh[q][2] = __double2float_rn(a.nv[2 * a.ldn + k]);
+            ahi[q] = 0.f;
+            alo[q] = 0.f;
+        }
+        const float4 pc = a.pcaps[tile];
+        auto issue = [&](int64_t j, uint32_t gi) {
+            const int b = gi % kStages;
+            const int cls = classify(pc, a.scaps[j], a.d_far);
+            s_cls[b] = cls;
+            if (cls == kFar) {
+                mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Far32)));
+                bulk_g2s(sbuf + (size_t)b * S, a.far + j * S, (uint32_t)(S * sizeof(Far32)), &bars[b]);
+            } else {
+                mbar_arrive_expect_tx(&bars[b], 0u);
+            }
+        };
+        if (tid == 0) {
+            const int pro = nt < kStages ? nt : kStages;
+            for (int i = 0; i < pro; ++i) issue(j0 + i, g + i);
+        }
+        int i = 0;
+        for (; i < nt; ++i) {
+            const uint32_t gi = g + i;
+            const int buf = gi % kStages;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+                s_abort = 1;
+            } else if (s_cls[buf] == kFar) {
+                const Far32 *fr = sbuf + (size_t)buf * S;
+                float part[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) part[q] = 0.f;
+#pragma unroll 2
+                for (int s = 0; s < S; ++s) {
+                    const float4 ra = fr[s].a, rb = fr[s].b, rc = fr[s].c, rd = fr[s].d;
+#pragma unroll
+                    for (int q = 0; q < P; ++q) {
+                        const float hs = fmaf(nh[q][2], ra.z, fmaf(nh[q][1], ra.y, fmaf(nh[q][0], ra.x, ra.w)));
+                        const float B = fmaf(nh[q][2], rb.z, fmaf(nh[q][1], rb.y, fmaf(nh[q][0], rb.x, 1.f)));
+                        const float A2 = fmaf(nh[q][2], rc.z, fmaf(nh[q][1], rc.y, fmaf(nh[q][0], rc.x, rc.w)));
+                        const float B2 = fmaf(rd.x, B, rb.w);
+                        const float num = fmaf(B2, B2, fmaf(-A2, A2, rd.y));
+                        part[q] = fmaf(num, rcp_approx(B * hs), part[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < P; ++q) fold(ahi[q], alo[q], part[q]);
+            }
+            __syncthreads();
+            if (s_abort) break;
+            if (tid == 0 && i + kStages < nt) issue(j0 + i + kStages, gi + kStages);
+        }
+        if (s_abort) {
+            if (tid == 0) {
+                atomicOr(&a.st->bits, kStatTimeout);
+                drain<S>(bars, g, i, nt);
+            }
+            return;
+        }
+        g += nt;
+
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
+            const double v = (double)ahi[q] + (double)alo[q];
+            if (a.split == 1) {
+                const int64_t oi = a.outidx[k];
+                if (oi >= 0) a.theta[oi] = a.accumulate ? a.theta[oi] + v : v;
+            } else {
+                a.partial[(int64_t)kc * tot + k] = v;
+            }
+        }
+    }
+}
+
+// Near-field pass: per (pixel tile, segment chunk) item, the segment tiles that the far pass
+// skipped (class kMid or kChecked), found by a warp-wide scan of the tile classes; the result
+// is added to the chunk's partial (or to theta when there is one chunk) after the far pass.
+// Mid tiles use the float-pair form; checked tiles form B without cancellation and send pairs
+// with |d| < rho or B < b_min/1000 to FP64.
+template <int NT, int P, int S>
+__global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
+{
+    constexpr int TILE = NT * P;
+    constexpr size_t kStageBytes = S * (sizeof(Seg32) + sizeof(Far32));   // both record types
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *sbuf = smem;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    __shared__ int s_abort;
+    __shared__ int s_cls[kStages];
+    __shared__ int64_t s_j[kStages];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) {
+        for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    unsigned nearcnt = 0, zerocnt = 0;
+    uint32_t g = 0;
+    const int64_t n_items = a.ntiles * a.split;
+    const int64_t tot = a.ntiles * TILE;
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int64_t tile = item / a.split;
+        const int kc = (int)(item - tile * a.split);
+        const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
         float nh[P][3], nl[P][3], ahi[P], alo[P];
         double a64[P];
-        unsigned valid = 0;  // padding slots are computed but neither written nor counted
+        unsigned valid = 0;
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
@@ -63,141 +191,181 @@ __global__ void __launch_bounds__(NT, (P >= 8 ? 1 : (NT >= 256 ? 2 : 4))) k_map_
             a64[q] = 0.0;
         }
         const float4 pc = a.pcaps[tile];
-
-        if (tid == 0) {
-            const int pro = nt < kStages ? nt : kStages;
-            for (int i = 0; i < pro; ++i) issue_tile<Seg32, S>(sbuf, bars, a.s32, j0 + i, g + i);
-        }
+        // warp 0 finds the next segment tile of this chunk at or after `pos` that is not far;
+        // lane 0 issues it
+        int64_t pos = j0;
+        auto issue_next = [&](uint32_t gi) {
+            int64_t found = -1;
+            int cls = kFar;
+            while (pos < j1) {
+                const int64_t jj = pos + lane;
+                const int c = jj < j1 ? classify(pc, a.scaps[jj], a.d_far) : kFar;
+                const unsigned m = __ballot_sync(0xffffffffu, c != kFar);
+                if (m) {
+                    const int l = __ffs(m) - 1;
+                    found = pos + l;
+                    cls = __shfl_sync(0xffffffffu, c, l);
+                    pos = found + 1;
+                    break;
+                }
+                pos += 32;
+            }
+            if (lane == 0) {
+                const int b = gi % kStages;
+                s_j[b] = found;
+                s_cls[b] = cls;
+                if (found >= 0) {
+                    unsigned char *dst = sbuf + (size_t)b * kStageBytes;
+                    mbar_arrive_expect_tx(&bars[b], (uint32_t)kStageBytes);
+                    bulk_g2s(dst, a.s32 + found * S, (uint32_t)(S * sizeof(Seg32)), &bars[b]);
+                    bulk_g2s(dst + S * sizeof(Seg32), a.far + found * S, (uint32_t)(S * sizeof(Far32)), &bars[b]);
+                } else {
+                    mbar_arrive_expect_tx(&bars[b], 0u);
+                }
+            }
+        };
+        if (w == 0)
+            for (int i = 0; i < kStages; ++i) issue_next(g + i);
         int i = 0;
-        for (; i < nt; ++i) {
+        for (;; ++i) {
             const uint32_t gi = g + i;
             const int buf = gi % kStages;
+            // the stage's tile index is read before the barrier: warp 0 rewrites the slot after it
+            int64_t j = -1;
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
                 s_abort = 1;
             } else {
-                const int64_t j = j0 + i;
-                const SegCap sc = a.scaps[j];
-                const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
-                const float gap = sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w;  // lower bound of |d|
-                // B = 1 + n.Xdot >= b_min for every pair unless the pixel cap meets the tile's beam cap
-                const float bx = pc.x - sc.b.x, by = pc.y - sc.b.y, bz = pc.z - sc.b.z;
-                const bool fast_b = sc.b.w < 0.f || sqrtf(bx * bx + by * by + bz * bz) > pc.w + sc.b.w;
-                const bool near = (gap < sc.r.x) || !fast_b;
-                const bool far = fast_b && (gap >= a.d_far);
-                const Seg32 *sb = sbuf + buf * S;
-                float part[P];
+                j = s_j[buf];
+                if (j >= 0) {
+                    const int cls = s_cls[buf];
+                    const Seg32 *sb = reinterpret_cast<const Seg32 *>(sbuf + (size_t)buf * kStageBytes);
+                    const Far32 *fr = reinterpret_cast<const Far32 *>(sbuf + (size_t)buf * kStageBytes +
+                                                                      S * sizeof(Seg32));
+                    float part[P];
 #pragma unroll
-                for (int q = 0; q < P; ++q) part[q] = 0.f;
-                if (far) {
-                    // |d| >= d_far for every pair: d.d/2 = 1 - n.Xhat, Xdot.d = B - e, X'.d = A - f
-#pragma unroll 2
-                    for (int s = 0; s < S; ++s) {
-                        const float4 ra = sb[s].a, rd = sb[s].d, re = sb[s].e;
-                        const float ch = 0.5f * ra.w;
+                    for (int q = 0; q < P; ++q) part[q] = 0.f;
+                    if (cls == kMid) {
+                        // per warp and sample: the far-field form when every pair of the warp has
+                        // 1 - n.Xhat >= d_far^2/2 (with a margin for its FP32 rounding)
+                        const float hmin = 0.5f * a.d_far * a.d_far * 1.001f + 1e-6f;
+                        for (int s = 0; s < S; ++s) {
+                            const float4 ra = sb[s].a;
+                            float h[P];
+                            bool ok = true;
 #pragma unroll
-                        for (int q = 0; q < P; ++q) {
-                            const float h = fmaf(-nh[q][2], ra.z, fmaf(-nh[q][1], ra.y, fmaf(-nh[q][0], ra.x, 1.f)));
-                            const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
-                            const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
-                            const float Pd = B - rd.w;
-                            const float Qd = A - re.w;
-                            const float num = fmaf(B, Pd, -A * Qd);
-                            const float r = rcp_approx(B * h);
-                            part[q] = fmaf(ch * num, r, part[q]);
-                        }
-                    }
-                } else if (!near) {
-#pragma unroll 2
-                    for (int s = 0; s < S; ++s) {
-                        const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e;
+                            for (int q = 0; q < P; ++q) {
+                                h[q] = fmaf(-nh[q][2], ra.z, fmaf(-nh[q][1], ra.y, fmaf(-nh[q][0], ra.x, 1.f)));
+                                ok = ok && (h[q] >= hmin);
+                            }
+                            if (__all_sync(0xffffffffu, ok)) {
+                                const float4 fa = fr[s].a, fb = fr[s].b, fc = fr[s].c, fd = fr[s].d;
 #pragma unroll
-                        for (int q = 0; q < P; ++q) {
-                            const float dx = (nh[q][0] - ra.x) + (nl[q][0] - rb.x);
-                            const float dy = (nh[q][1] - ra.y) + (nl[q][1] - rb.y);
-                            const float dz = (nh[q][2] - ra.z) + (nl[q][2] - rb.z);
-                            const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            const float Pd = fmaf(rd.z, dz, fmaf(rd.y, dy, rd.x * dx));
-                            const float Qd = fmaf(re.z, dz, fmaf(re.y, dy, re.x * dx));
-                            const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
-                            const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
-                            const float num = fmaf(B, Pd, -A * Qd);
-                            const float r = rcp_approx(B * Q);
-                            part[q] = fmaf(ra.w * num, r, part[q]);
-                        }
-                    }
-                } else {
-                    // checked loop: two-float d, B formed without cancellation near -Xdot/|Xdot|;
-                    // pairs with |d| < rho or B < b_min/1000 go to FP64
-                    const float b_tiny = a.b_min * 1e-3f;
-                    for (int s = 0; s < S; ++s) {
-                        const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e, rk = sb[s].k;
-                        const float hv = fmaf(-0.5f, rk.w, 0.5f);   // |Xdot| / 2
-                        unsigned mask = 0;
+                                for (int q = 0; q < P; ++q) {
+                                    const float hs = fmaf(nh[q][2], fa.z, fmaf(nh[q][1], fa.y, fmaf(nh[q][0], fa.x, fa.w)));
+                                    const float B = fmaf(nh[q][2], fb.z, fmaf(nh[q][1], fb.y, fmaf(nh[q][0], fb.x, 1.f)));
+                                    const float A2 =
+                                        fmaf(nh[q][2], fc.z, fmaf(nh[q][1], fc.y, fmaf(nh[q][0], fc.x, fc.w)));
+                                    const float B2 = fmaf(fd.x, B, fb.w);
+                                    const float num = fmaf(B2, B2, fmaf(-A2, A2, fd.y));
+                                    part[q] = fmaf(num, rcp_approx(B * hs), part[q]);
+                                }
+                                continue;
+                            }
+                            const float4 rb = sb[s].b, rd = sb[s].d, re = sb[s].e;
 #pragma unroll
-                        for (int q = 0; q < P; ++q) {
-                            const float dx = (nh[q][0] - ra.x) + (nl[q][0] - rb.x);
-                            const float dy = (nh[q][1] - ra.y) + (nl[q][1] - rb.y);
-                            const float dz = (nh[q][2] - ra.z) + (nl[q][2] - rb.z);
-                            const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            const float Pd = fmaf(rd.z, dz, fmaf(rd.y, dy, rd.x * dx));
-                            const float Qd = fmaf(re.z, dz, fmaf(re.y, dy, re.x * dx));
-                            const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
-                            const float wx = nh[q][0] + rk.x, wy = nh[q][1] + rk.y, wz = nh[q][2] + rk.z;
-                            const float B = fmaf(hv, fmaf(wz, wz, fmaf(wy, wy, wx * wx)), rk.w);
-                            if (Q < rb.w || B < b_tiny) {
-                                mask |= 1u << q;
-                            } else {
+                            for (int q = 0; q < P; ++q) {
+                                const float dx = (nh[q][0] - ra.x) + (nl[q][0] - rb.x);
+                                const float dy = (nh[q][1] - ra.y) + (nl[q][1] - rb.y);
+                                const float dz = (nh[q][2] - ra.z) + (nl[q][2] - rb.z);
+                                const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                                const float Pd = fmaf(rd.z, dz, fmaf(rd.y, dy, rd.x * dx));
+                                const float Qd = fmaf(re.z, dz, fmaf(re.y, dy, re.x * dx));
+                                const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
+                                const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
                                 const float num = fmaf(B, Pd, -A * Qd);
                                 const float r = rcp_approx(B * Q);
                                 part[q] = fmaf(ra.w * num, r, part[q]);
                             }
                         }
-                        if (__any_sync(0xffffffffu, mask != 0)) {
-                            const Seg64 g64 = a.s64[j * S + s];
+                    } else {
+                        const float b_tiny = a.b_min * 1e-3f;
+                        for (int s = 0; s < S; ++s) {
+                            const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e, rk = sb[s].k;
+                            const float hv = fmaf(-0.5f, rk.w, 0.5f);   // |Xdot| / 2
+                            unsigned mask = 0;
 #pragma unroll
                             for (int q = 0; q < P; ++q) {
-                                if (mask & (1u << q)) {
-                                    const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
-                                    unsigned z = 0;
-                                    a64[q] += pair64(a.nv[k], a.nv[a.ldn + k], a.nv[2 * a.ldn + k], g64, z);
-                                    if (valid & (1u << q)) {
-                                        zerocnt += z;
-                                        ++nearcnt;
+                                const float dx = (nh[q][0] - ra.x) + (nl[q][0] - rb.x);
+                                const float dy = (nh[q][1] - ra.y) + (nl[q][1] - rb.y);
+                                const float dz = (nh[q][2] - ra.z) + (nl[q][2] - rb.z);
+                                const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                                const float Pd = fmaf(rd.z, dz, fmaf(rd.y, dy, rd.x * dx));
+                                const float Qd = fmaf(re.z, dz, fmaf(re.y, dy, re.x * dx));
+                                const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
+                                const float wx = nh[q][0] + rk.x, wy = nh[q][1] + rk.y, wz = nh[q][2] + rk.z;
+                                const float B = fmaf(hv, fmaf(wz, wz, fmaf(wy, wy, wx * wx)), rk.w);
+                                if (Q < rb.w || B < b_tiny) {
+                                    mask |= 1u << q;
+                                } else {
+                                    const float num = fmaf(B, Pd, -A * Qd);
+                                    const float r = rcp_approx(B * Q);
+                                    part[q] = fmaf(ra.w * num, r, part[q]);
+                                }
+                            }
+                            if (__any_sync(0xffffffffu, mask != 0)) {
+                                const Seg64 g64 = a.s64[j * S + s];
+#pragma unroll
+                                for (int q = 0; q < P; ++q) {
+                                    if (mask & (1u << q)) {
+                                        const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
+                                        unsigned z = 0;
+                                        a64[q] += pair64(a.nv[k], a.nv[a.ldn + k], a.nv[2 * a.ldn + k], g64, z);
+                                        if (valid & (1u << q)) {
+                                            zerocnt += z;
+                                            ++nearcnt;
+                                        }
                                     }
                                 }
                             }
                         }
                     }
-                }
 #pragma unroll
-                for (int q = 0; q < P; ++q) fold(ahi[q], alo[q], part[q]);
+                    for (int q = 0; q < P; ++q) fold(ahi[q], alo[q], part[q]);
+                }
             }
             __syncthreads();
-            if (s_abort) break;
-            if (tid == 0 && i + kStages < nt) issue_tile<Seg32, S>(sbuf, bars, a.s32, j0 + i + kStages, gi + kStages);
+            if (s_abort || j < 0) break;
+            if (w == 0) issue_next(gi + kStages);
         }
         if (s_abort) {
-            if (tid == 0) {
-                atomicOr(&a.st->bits, kStatTimeout);
-                drain<S>(bars, g, i, nt);
-            }
+            if (tid == 0) atomicOr(&a.st->bits, kStatTimeout);
+            // every issued stage after this one was either a copy or a zero-byte arrive
+            if (tid == 0) drain<S>(bars, g, i, i + kStages);
             return;
         }
-        g += nt;
+        // stages issued after the end marker (zero-byte arrives) complete their phases; consume them
+        for (int m = i + 1; m < i + kStages; ++m) {
+            const uint32_t gm = g + m;
+            (void)__all_sync(0xffffffffu, mbar_wait_bounded(&bars[gm % kStages], (gm / kStages) & 1));
+        }
+        __syncthreads();
+        g += i + kStages;
 
+        // added after the far pass of the same chunk: into the chunk's partial, or into theta
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
             const double v = ((double)ahi[q] + (double)alo[q]) + a64[q];
-            if (a.split == 1) {
-                const int64_t oi = a.outidx[k];
-                if (oi >= 0) a.theta[oi] = a.accumulate ? a.theta[oi] + v : v;
-            } else {
-                a.partial[(int64_t)kc * tot + k] = v;
+            if (v != 0.0) {
+                if (a.split == 1) {
+                    const int64_t oi = a.outidx[k];
+                    if (oi >= 0) a.theta[oi] += v;
+                } else {
+                    a.partial[(int64_t)kc * tot + k] += v;
+                }
             }
         }
     }
-    // per-warp counters
     for (int o = 16; o > 0; o >>= 1) {
         nearcnt += __shfl_xor_sync(0xffffffffu, nearcnt, o);
         zerocnt += __shfl_xor_sync(0xffffffffu, zerocnt, o);
@@ -319,24 +487,31 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int64_t to
 // ------------------------------------------------------------------------------------
 // Variant table and launchers
 // ------------------------------------------------------------------------------------
+// (threads, pixels per thread, segments per stage, minimum resident CTAs per SM)
 #define ISW_F32_VARIANTS(X) \
-    X(256, 4, 64)           \
-    X(256, 2, 64)           \
-    X(128, 4, 64)           \
-    X(256, 8, 32)           \
-    X(128, 8, 32)
+    X(256, 4, 64, 2)        \
+    X(256, 2, 64, 2)        \
+    X(128, 4, 64, 4)        \
+    X(256, 8, 32, 1)        \
+    X(128, 8, 32, 1)        \
+    X(256, 4, 64, 3)        \
+    X(128, 4, 64, 6)        \
+    X(128, 4, 32, 5)
 
 namespace {
 struct VEntry {
     Variant v;
-    const void *fn;
+    const void *fn;       // far-field pass
+    const void *near_fn;  // near-field pass with the same tiling
 };
-#define ISW_ENTRY(NT, P, S) {{NT, P, S, 32, (NT / 32) * P}, (const void *)&k_map_f32c<NT, P, S>},
+#define ISW_ENTRY(NT, P, S, MB)                                                                                   \
+    {{NT, P, S, 32, (NT / 32) * P}, (const void *)&k_map_f32c<NT, P, S, MB>, (const void *)&k_map_f32c_near<NT, P, S>},
 const VEntry kF32[] = {ISW_F32_VARIANTS(ISW_ENTRY)};
 #undef ISW_ENTRY
 constexpr int kF64NT = 128, kF64P = 2, kF64S = 32;
 
-size_t smem_f32(int S) { return kStages * S * sizeof(Seg32) + kStages * sizeof(uint64_t); }
+size_t smem_f32(int S) { return kStages * S * sizeof(Far32) + kStages * sizeof(uint64_t); }
+size_t smem_near(int S) { return kStages * S * (sizeof(Seg32) + sizeof(Far32)) + kStages * sizeof(uint64_t); }
 size_t smem_f64(int S) { return kStages * S * sizeof(Seg64) + kStages * sizeof(uint64_t); }
 }  // namespace
 
@@ -366,6 +541,21 @@ void launch_map_f32c(int idx, const MapArgs &a, int grid, cudaStream_t s)
     const Variant v = kF32[idx].v;
     void *args[] = {(void *)&a};
     cudaLaunchKernel(kF32[idx].fn, dim3(grid), dim3(v.threads), args, smem_f32(v.seg_tile), s);
+}
+
+// The near-field pass runs the same pixel tiling and segment tiles as the far pass.
+void launch_map_f32c_near(int idx, const MapArgs &a, int num_sms, cudaStream_t s)
+{
+    const Variant v = kF32[idx].v;
+    void *args[] = {(void *)&a};
+    const void *fn = kF32[idx].near_fn;
+    const size_t sm = smem_near(v.seg_tile);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, v.threads, sm);
+    const int64_t slots = (int64_t)(nb > 0 ? nb : 1) * num_sms;
+    const int64_t items = a.ntiles * a.split;
+    const int grid = (int)(items < slots ? items : slots);
+    cudaLaunchKernel(fn, dim3(grid), dim3(v.threads), args, sm, s);
 }
 
 void launch_map_f64(const MapArgs &a, int grid, cudaStream_t s)

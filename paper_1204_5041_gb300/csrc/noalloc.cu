@@ -6,7 +6,7 @@
 // synchronisation cudaMalloc and cudaFree may perform.  isw_map needs an isw_ctx, whose
 // creation and workspace growth allocate; this entry point needs neither.
 //
-// Its scratch (pixel table, sample records, tile caps, segment-chunk partials and the
+// Its scratch (pixel table, sample records, far-field records, tile caps, segment-chunk partials and the
 // device status word) lives in one file-scope __device__ array of kStaticScratchBytes.
 // Every GPU that loads the library holds that array until the process exits.  All calls
 // share it and it keeps the previous call's contents: each call clears the status word and
@@ -98,6 +98,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     off[4] = at; at += up256((size_t)n_pad * sizeof(Seg32));
     off[5] = at; at += up256((size_t)n_pad * sizeof(Seg64));
     off[6] = at; at += up256((size_t)nst * sizeof(SegCap));
+    const size_t off_far = at; at += up256((size_t)n_pad * sizeof(Far32));
     off[7] = at;
     if (at > kStaticScratchBytes) return ISW_EINVAL;  // problem too large for the static scratch
     const int64_t room = (int64_t)((kStaticScratchBytes - at) / ((size_t)tot * sizeof(double)));
@@ -137,7 +138,8 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     launch_pixel_table(nside, full ? 0 : 1, pix0, npix, nullptr, v.tx, v.ty, ntiles, nv, tot, outidx, pcaps, st, s);
-    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, s32, s64, st, s);
+    Far32 *far = (Far32 *)(b + off_far);
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, s32, s64, far, st, s);
     launch_seg_caps(s32, s64, n, n_pad, S, 0.01f, scaps, s);
     MapArgs a;
     a.nv = nv;
@@ -147,17 +149,19 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.ntiles = ntiles;
     a.s32 = s32;
     a.s64 = s64;
+    a.far = far;
     a.scaps = scaps;
     a.nst = nst;
     a.split = split;
     a.b_min = 0.01f;
-    a.d_far = 0.4f;
+    a.d_far = 0.25f;
     a.theta = theta_out;
     a.partial = split > 1 ? partial : nullptr;
     a.accumulate = 0;
     a.st = st;
     const int64_t items = ntiles * split;
     launch_map_f32c(0, a, (int)(items < slots ? items : slots), s);
+    launch_map_f32c_near(0, a, sms, s);
     if (split > 1) launch_reduce_partials(a, tile, s);
     return cudaGetLastError() == cudaSuccess ? ISW_OK : ISW_ECUDA;
 }
