@@ -116,6 +116,47 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+def weak_scaling_value(pairs_per_rank_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job pairs/s: every rank maps its own network; the slowest rank sets the time."""
+    return world * pairs_per_rank_step * steps / (max_ms / 1e3)
+
+
+def max_over_ranks(ms: float, dist=None, device=None) -> float:
+    """Largest timed-region duration over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms)
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def kernel_sources_sha1() -> str:
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in ("map.cu", "pipeline.cuh", "isw_internal.cuh", "pack.cu"):
+        with open(os.path.join(ROOT, "paper_1204_5041_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(variant: int):
+    """DRAM bytes per step of the pair kernels from the committed ncu summary, when it was taken on
+    the current kernel sources and the same variant; else None."""
+    import re
+
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "launches_nside512_200k_seg.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_step=(\d+) variant=(-?\d+) csrc_sha1=([0-9a-f]+)", txt)
+    if not m or int(m.group(2)) != variant or m.group(3) != kernel_sources_sha1():
+        return None
+    return int(m.group(1))
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -190,16 +231,13 @@ def run_gpu(args):
     ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     map_ms, map_launches, all_launches = ctx.timing(reset=True)
     ctx.set_param(isw.PARAM_TIMING, 0)
+    variant_used = int(ctx.get_param(isw.PARAM_VARIANT))
     r, counts = ctx.check_status()
     if r != isw.OK:
         raise RuntimeError(f"device status {r} in the timed region: {ctx.last_error()}")
-    total_ms = float(sum(ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(ms)), dist if ws > 1 else None, dev)
     pairs_step = w.npix * w.n
-    value = ws * pairs_step * args.steps / (total_ms / 1e3)
+    value = weak_scaling_value(pairs_step, args.steps, ws, total_ms)
 
     # ---- end to end through the public API: pinned host inputs in, map out, every step
     theta_h = torch.empty(w.npix, dtype=torch.float64).pin_memory()
@@ -273,7 +311,8 @@ def run_gpu(args):
     map_avg_ms = map_ms / max(map_launches, 1)
     achieved = FLOPS_PER_PAIR * pairs_step / (map_avg_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "pair kernels: isw::k_map_f32c (far field) + k_map_f32c_near, autotuned variant",
+            "traffic": (profiled_traffic(variant_used) if args.nside is None else None),
+            "kernel": f"pair kernels: isw::k_map_f32c (far field) + k_map_f32c_near + chunk reduce, variant {variant_used}",
             "flops_per_pair": FLOPS_PER_PAIR, "kernel_ms": map_avg_ms, "kernel_launches": map_launches,
             "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz (max SM clock)"}
     out = {

@@ -101,6 +101,11 @@ int isw_check_status(isw_ctx *ctx, void *stream, int64_t *counts);
  * isw_get_timing. */
 int isw_set_param(isw_ctx *ctx, int key, double value);
 
+/* Read a tunable into *value (host pointer).  For ISW_PARAM_VARIANT the value is the FP32
+ * kernel variant the last FP32 map of this context used (the override, the autotuner's pick or
+ * the default), or -1 before any FP32 map. */
+int isw_get_param(const isw_ctx *ctx, int key, double *value);
+
 /* Timing of the pair kernel (ISW_PARAM_TIMING = 1): synchronises the recorded events and
  * returns in *ms the summed device time of the pair-kernel launches recorded since the last
  * reset, in *pair_launches their number and in *all_launches the number of kernels of any

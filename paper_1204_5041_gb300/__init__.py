@@ -64,6 +64,7 @@ def lib():
                 "isw_last_error": (ctypes.c_char_p, [_vp]),
                 "isw_check_status": (_i32, [_vp, _vp, ctypes.POINTER(_i64)]),
                 "isw_set_param": (_i32, [_vp, _i32, _dbl]),
+                "isw_get_param": (_i32, [_vp, _i32, ctypes.POINTER(_dbl)]),
                 "isw_get_timing": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                           _i32]),
                 "hp_pix2vec_ring": (_i32, [_vp, _i64, _i64, _i64, _vp, _vp, _i64, _vp]),
@@ -120,6 +121,11 @@ class Context:
 
     def set_param(self, key: int, value: float):
         self.check(lib().isw_set_param(self._h, int(key), float(value)))
+
+    def get_param(self, key: int) -> float:
+        v = _dbl()
+        self.check(lib().isw_get_param(self._h, int(key), ctypes.byref(v)))
+        return v.value
 
     def timing(self, reset: bool = True):
         """(summed device ms of the timed pair-kernel launches, pair-kernel launches, all kernel

@@ -197,6 +197,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
         if (c->tile_override >= 0 && c->tile_override < num_f32_variants()) vidx = c->tile_override;
         else if (c->tuned_nside == nside && c->tuned_n == n) vidx = c->auto_variant;
     }
+    if (prec == ISW_F32C && !c->capturing) c->last_variant = vidx;
     const Variant v = prec == ISW_F32C ? f32_variant(vidx) : f64_variant();
     const int S = v.seg_tile;
     const PixelPlan pp = plan_pixels(nside, pix0, npix, pix_list, v);
@@ -294,6 +295,7 @@ int isw_create(isw_ctx **out, int device)
     c->split_override = 0;
     c->tile_override = -1;
     c->tuned_nside = -1;
+    c->last_variant = -1;
     c->meta_nshell = -1;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -360,6 +362,20 @@ int isw_set_param(isw_ctx *c, int key, double value)
         return ISW_OK;
     default:
         return set_err(c, ISW_EINVAL, "unknown parameter key %d", key);
+    }
+}
+
+int isw_get_param(const isw_ctx *c, int key, double *value)
+{
+    if (!c || !value) return ISW_EINVAL;
+    switch (key) {
+    case ISW_PARAM_NEAR_K: *value = c->near_k; return ISW_OK;
+    case ISW_PARAM_B_MIN: *value = c->b_min; return ISW_OK;
+    case ISW_PARAM_SPLIT: *value = c->split_override; return ISW_OK;
+    case ISW_PARAM_VARIANT: *value = c->last_variant; return ISW_OK;
+    case ISW_PARAM_TIMING: *value = c->timing; return ISW_OK;
+    case ISW_PARAM_D_FAR: *value = c->d_far; return ISW_OK;
+    default: return ISW_EINVAL;
     }
 }
 

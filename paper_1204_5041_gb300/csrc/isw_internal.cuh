@@ -338,6 +338,7 @@ struct isw_ctx {
     cudaEvent_t *ev;    // 2 * kMaxTimed events, created on first use
     // FP32 variant picked by the autotuner for (tuned_nside, tuned_n); used when no override
     int auto_variant;
+    int last_variant;   // FP32 variant used by the last FP32 map
     int64_t tuned_nside, tuned_n;
     // batched path: shell metadata last uploaded, and one captured graph
     uint64_t meta_hash;

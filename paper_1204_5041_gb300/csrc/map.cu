@@ -496,7 +496,10 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int64_t to
     X(128, 8, 32, 1)        \
     X(256, 4, 64, 3)        \
     X(128, 4, 64, 6)        \
-    X(128, 4, 32, 5)
+    X(128, 4, 32, 5)        \
+    X(128, 4, 128, 4)       \
+    X(128, 8, 64, 3)        \
+    X(256, 8, 64, 2)
 
 namespace {
 struct VEntry {
@@ -511,6 +514,11 @@ const VEntry kF32[] = {ISW_F32_VARIANTS(ISW_ENTRY)};
 constexpr int kF64NT = 128, kF64P = 2, kF64S = 32;
 
 size_t smem_f32(int S) { return kStages * S * sizeof(Far32) + kStages * sizeof(uint64_t); }
+// Stages above the default 48 KB of dynamic shared memory need the opt-in attribute.
+void allow_smem(const void *fn, size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 size_t smem_near(int S) { return kStages * S * (sizeof(Seg32) + sizeof(Far32)) + kStages * sizeof(uint64_t); }
 size_t smem_f64(int S) { return kStages * S * sizeof(Seg64) + kStages * sizeof(uint64_t); }
 }  // namespace
@@ -524,6 +532,7 @@ int map_f32c_slots(int idx, int num_sms)
 {
     int nb = 0;
     const Variant v = kF32[idx].v;
+    allow_smem(kF32[idx].fn, smem_f32(v.seg_tile));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kF32[idx].fn, v.threads, smem_f32(v.seg_tile));
     return (nb > 0 ? nb : 1) * num_sms;
 }
@@ -540,6 +549,7 @@ void launch_map_f32c(int idx, const MapArgs &a, int grid, cudaStream_t s)
 {
     const Variant v = kF32[idx].v;
     void *args[] = {(void *)&a};
+    allow_smem(kF32[idx].fn, smem_f32(v.seg_tile));
     cudaLaunchKernel(kF32[idx].fn, dim3(grid), dim3(v.threads), args, smem_f32(v.seg_tile), s);
 }
 
@@ -550,6 +560,7 @@ void launch_map_f32c_near(int idx, const MapArgs &a, int num_sms, cudaStream_t s
     void *args[] = {(void *)&a};
     const void *fn = kF32[idx].near_fn;
     const size_t sm = smem_near(v.seg_tile);
+    allow_smem(fn, sm);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, v.threads, sm);
     const int64_t slots = (int64_t)(nb > 0 ? nb : 1) * num_sms;

@@ -40,7 +40,7 @@ def _err(got, ref):
 
 
 def isw_num_variants():
-    return 8
+    return 11
 
 
 def _status_ok(isw):
