@@ -181,7 +181,7 @@ void timing_end(isw_ctx *c, int k, cudaStream_t s)
 // Shared body of isw_map: pixel table, sample records, caps, map kernel, partial reduce.
 int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list, const double *samples,
              int64_t n, int64_t ld, const double *x_obs, double GU, int prec, int accumulate, double *theta,
-             cudaStream_t s)
+             cudaStream_t s, int64_t tune_waves = 0, int64_t *tuned_pixels = nullptr)
 {
     const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
     if (npix == 0) return ISW_OK;
@@ -251,8 +251,15 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.partial = split > 1 ? (double *)c->ws[kWsPartial] : nullptr;
     a.accumulate = accumulate;
     a.st = c->d_status;
-    const int64_t items = pp.ntiles * split;
+    // timing a variant: every k-th pixel tile (all its segment chunks), about tune_waves waves
+    a.tile_stride = 1;
+    if (tune_waves > 0) {
+        const int64_t want = tune_waves * slots / split;
+        a.tile_stride = want > 0 && pp.ntiles > want ? pp.ntiles / want : 1;
+    }
+    const int64_t items = (pp.ntiles + a.tile_stride - 1) / a.tile_stride * split;
     const int grid = (int)(items < slots ? items : slots);
+    if (tuned_pixels) *tuned_pixels = (pp.ntiles + a.tile_stride - 1) / a.tile_stride * (v.tx * v.ty);
     // the timed pair work: far pass (or the FP64 kernel), chunk reduce, near-field pass
     const int ti = timing_begin(c, s);
     if (prec == ISW_F32C) {
@@ -653,28 +660,30 @@ int isw_map_batched(isw_ctx *c, int64_t nside, const double *nodes, int64_t ld, 
                                     xo[1], xo[2], t_obs, tol, (double *)c->ws[kWsSamples], n, c->d_status, s);
             c->n_launch += 1;
         }
-        const int64_t nt = n < 16384 ? n : 16384;   // prefix of the samples used for timing
+        // every variant maps all samples onto a strided subset of the pixel tiles (~4 waves)
         if ((r = ensure_ws(c, kWsMisc, (size_t)npix * sizeof(double)))) return r;
         double *scratch_theta = (double *)c->ws[kWsMisc];
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        float best = 1e30f;
+        double best = 1e300;   // device ms per processed pixel slot
         int best_v = 0;
         const int saved_timing = c->timing;
         c->timing = 0;
         for (int v = 0; v < num_f32_variants(); ++v) {
             c->tile_override = v;
-            float tv = 0.f;
+            double tv = 0.0;
+            int64_t px = 1;
             for (int rep = 0; rep < 2; ++rep) {
                 cudaEventRecord(e0, s);
-                r = map_impl(c, nside, 0, npix, nullptr, samples, nt, lds, x_obs, GU, prec, 0, scratch_theta, s);
+                r = map_impl(c, nside, 0, npix, nullptr, samples, n, lds, x_obs, GU, prec, 0, scratch_theta, s, 4,
+                             &px);
                 cudaEventRecord(e1, s);
                 if (r) break;
                 cudaEventSynchronize(e1);
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (rep == 1) tv = ms;
+                if (rep == 1) tv = (double)ms / (double)(px > 0 ? px : 1);
             }
             if (r) break;
             if (tv < best) {

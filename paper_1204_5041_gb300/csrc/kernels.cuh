@@ -50,6 +50,7 @@ struct MapArgs {
     double *partial;         // [split][ntiles*tile] when split > 1
     int accumulate;
     DevStatus *st;
+    int64_t tile_stride;     // 1; > 1 only when timing variants: every tile_stride-th pixel tile
 };
 struct Variant {
     int threads, ppt, seg_tile, tx, ty;

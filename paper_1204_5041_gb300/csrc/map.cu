@@ -54,11 +54,11 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
     __syncthreads();
 
     uint32_t g = 0;
-    const int64_t n_items = a.ntiles * a.split;
+    const int64_t n_items = (a.ntiles + a.tile_stride - 1) / a.tile_stride * a.split;
     const int64_t tot = a.ntiles * TILE;
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int64_t tile = item / a.split;
-        const int kc = (int)(item - tile * a.split);
+        const int64_t tile = item / a.split * a.tile_stride;
+        const int kc = (int)(item % a.split);
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
         const int nt = (int)(j1 - j0);
 
@@ -167,11 +167,11 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
     __syncthreads();
     unsigned nearcnt = 0, zerocnt = 0;
     uint32_t g = 0;
-    const int64_t n_items = a.ntiles * a.split;
+    const int64_t n_items = (a.ntiles + a.tile_stride - 1) / a.tile_stride * a.split;
     const int64_t tot = a.ntiles * TILE;
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int64_t tile = item / a.split;
-        const int kc = (int)(item - tile * a.split);
+        const int64_t tile = item / a.split * a.tile_stride;
+        const int kc = (int)(item % a.split);
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
         float nh[P][3], nl[P][3], ahi[P], alo[P];
         double a64[P];
@@ -564,7 +564,7 @@ void launch_map_f32c_near(int idx, const MapArgs &a, int num_sms, cudaStream_t s
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, v.threads, sm);
     const int64_t slots = (int64_t)(nb > 0 ? nb : 1) * num_sms;
-    const int64_t items = a.ntiles * a.split;
+    const int64_t items = (a.ntiles + a.tile_stride - 1) / a.tile_stride * a.split;
     const int grid = (int)(items < slots ? items : slots);
     cudaLaunchKernel(fn, dim3(grid), dim3(v.threads), args, sm, s);
 }

@@ -159,6 +159,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.partial = split > 1 ? partial : nullptr;
     a.accumulate = 0;
     a.st = st;
+    a.tile_stride = 1;
     const int64_t items = ntiles * split;
     launch_map_f32c(0, a, (int)(items < slots ? items : slots), s);
     launch_map_f32c_near(0, a, sms, s);
