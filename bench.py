@@ -151,10 +151,11 @@ def profiled_traffic(variant: int):
         txt = open(os.path.join(ROOT, "profiles", "launches_nside512_200k_seg.md")).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_step=(\d+) variant=(-?\d+) csrc_sha1=([0-9a-f]+)", txt)
-    if not m or int(m.group(2)) != variant or m.group(3) != kernel_sources_sha1():
-        return None
-    return int(m.group(1))
+    sha = kernel_sources_sha1()
+    for tb, v, s in re.findall(r"traffic_bytes_per_step=(\d+) variant=(-?\d+) csrc_sha1=([0-9a-f]+)", txt):
+        if int(v) == variant and s == sha:
+            return int(tb)
+    return None
 
 
 def _dist():
