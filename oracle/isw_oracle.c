@@ -217,7 +217,9 @@ int or_pix2vec_ring(int64_t nside, int64_t pix0, int64_t n, const int64_t *pix,
  * a(u) = L/(2 pi m) (sin 2 pi m u/L, -cos 2 pi m u/L, 0) and
  * b(v) = L/(2 pi n) (sin 2 pi n v/L, -cos(psi) cos 2 pi n v/L, -sin(psi) cos 2 pi n v/L).
  * f(t) = |X(s,t) - x_obs| - (t_obs - t) is increasing; safeguarded Newton on the bracket
- * [t_obs - d - L/2, t_obs - d + L/2] (d = |c - x_obs|), stop when |f| <= tol.
+ * [t_obs - d - L/2, t_obs - d + L/2] (d = |c - x_obs|): a bisection replaces the Newton step
+ * when it leaves the bracket or is longer than half the step two iterations back; stop when
+ * |f| <= tol.
  * ---------------------------------------------------------------------------------- */
 static void burden_eval(const double *P, int64_t ldp, int64_t id, double sigma, double t,
                         double X[3], double Xd[3], double Xp[3])
@@ -305,6 +307,7 @@ int or_lightcone(int mode, const double *nodes, int64_t n, int64_t ld,
                 double d = sqrt((cx * cx + cy * cy) + cz * cz);
                 double halfL = 0.5 * P[12 * ldp + id];
                 double lo = (t_obs - d) - halfL, hi = (t_obs - d) + halfL;
+                double step1 = hi - lo, step2 = hi - lo;   /* last two step lengths */
                 t = t_obs - d;
                 st = OR_ENOCONV;
                 for (int it = 0; it < max_iter; ++it) {
@@ -323,7 +326,11 @@ int or_lightcone(int mode, const double *nodes, int64_t n, int64_t ld,
                     if (f < 0.0) lo = t; else hi = t;
                     double fp = 1.0 + ((r[0] * Xd[0] + r[1] * Xd[1]) + r[2] * Xd[2]) / rn;
                     double tn = t - f / fp;
-                    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+                    /* bisect when Newton leaves the bracket or does not at least halve the step
+                       taken two iterations earlier (stops two-cycles between the bracket ends) */
+                    if (!(tn > lo && tn < hi) || fabs(tn - t) > 0.5 * step2) tn = 0.5 * (lo + hi);
+                    step2 = step1;
+                    step1 = fabs(tn - t);
                     if (it + 1 < max_iter) t = tn;
                 }
             }

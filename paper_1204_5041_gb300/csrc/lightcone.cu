@@ -92,10 +92,12 @@ __device__ __forceinline__ int solve_node(int mode, const double *__restrict__ n
             const double d = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
             const double halfL = dmul(0.5, P[12 * ldp + id]);
             double lo = dsub(dsub(t_obs, d), halfL), hi = dadd(dsub(t_obs, d), halfL);
+            double step1 = dsub(hi, lo), step2 = dsub(hi, lo);   // last two step lengths
             t = dsub(t_obs, d);
             st = ISW_ENOCONV;
             // f(t) = |X(s, t) - x_obs| - (t_obs - t) is increasing (f' = 1 + rhat.Xdot > 0):
-            // Newton steps, replaced by bisection when they leave the bracket
+            // Newton steps, replaced by bisection when they leave the bracket or fail to halve
+            // the step taken two iterations earlier
             for (int it = 0; it < max_iter; ++it) {
                 burden_worldsheet(P, ldp, id, sigma, t, X, Xd, Xp);
                 const double r[3] = {dsub(X[0], xo0), dsub(X[1], xo1), dsub(X[2], xo2)};
@@ -112,7 +114,11 @@ __device__ __forceinline__ int solve_node(int mode, const double *__restrict__ n
                 if (f < 0.0) lo = t; else hi = t;
                 const double fp = dadd(1.0, ddiv(dadd(dadd(dmul(r[0], Xd[0]), dmul(r[1], Xd[1])), dmul(r[2], Xd[2])), rn));
                 double tn = dsub(t, ddiv(f, fp));
-                if (!(tn > lo && tn < hi)) tn = dmul(0.5, dadd(lo, hi));
+                // bisect when Newton leaves the bracket or does not at least halve the step taken
+                // two iterations earlier (stops two-cycles between the bracket ends)
+                if (!(tn > lo && tn < hi) || fabs(dsub(tn, t)) > dmul(0.5, step2)) tn = dmul(0.5, dadd(lo, hi));
+                step2 = step1;
+                step1 = fabs(dsub(tn, t));
                 if (it + 1 < max_iter) t = tn;
             }
         }

@@ -80,6 +80,22 @@ def test_lightcone_bitexact(isw):
     assert _status_ok(isw)[0] == isw.OK
 
 
+def test_lightcone_bitexact_nside4096_workload(isw):
+    """All 2e6 nodes of the 1024-shell workload, shell by shell, bit-identical to the oracle."""
+    w = synth.config(4, seed=1)
+    ref, _, st_ref = oracle.lightcone_workload(w)
+    assert np.all(st_ref == 0)
+    nodes = _d(w.nodes)
+    P = _d(w.loop_params)
+    out = torch.empty_like(nodes)
+    for k in range(w.nshell):
+        a, b = int(w.shell_off[k]), int(w.shell_off[k + 1])
+        if b > a:
+            isw.lightcone_intersect(int(w.mode[k]), nodes[:, a:b], P, float(w.t_box[k]), out=out[:, a:b])
+    assert _status_ok(isw)[0] == isw.OK
+    assert np.array_equal(out.cpu().numpy().view(np.int64), ref.view(np.int64))
+
+
 def test_lightcone_status_codes(isw):
     w = synth.config(0, seed=4)
     nodes = w.nodes[:, :64].copy()

@@ -154,3 +154,15 @@ def test_burden_iteration_cap(oracle_lib, loops):
     bad[0, 0] = 10 ** 6          # loop id out of range
     _, _, st = oracle_lib.lightcone(1, bad, loops.loop_params)
     assert st[0] == 1 and st[1] == 0
+
+
+def test_burden_no_two_cycles_large_workload(oracle_lib):
+    """Every node of the Nside=4096 workload (2e6 samples, 1024 shells) converges: nodes 659026 and
+    1117799 of seed 1 once alternated between the bracket ends under plain safeguarded Newton."""
+    w = synth.config(4, seed=1)
+    S, tau, st = oracle_lib.lightcone_workload(w)
+    assert np.all(st == 0)
+    R = np.linalg.norm(S[0:3], axis=0)
+    assert np.max(np.abs(R - (T_OBS - tau))) <= _tol() * 1.0001
+    for node in (659026, 1117799):
+        assert w.mode[np.searchsorted(w.shell_off, node, side="right") - 1] == oracle_lib.BURDEN
