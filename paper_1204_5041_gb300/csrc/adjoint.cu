@@ -25,7 +25,15 @@ namespace isw {
 
 constexpr int kAcc = 13;
 
-// FP64 pair derivative sums (used by the FP64 kernel and for the FP32 kernel's near field)
+// Per-pair derivative sums.  With d = n - Xhat, Q = d.d, u = Xdot - (A/B) X', T = u.d / Q and
+// eta = 2T/Q, the n-dependent parts of the three gradients are accumulated as vectors along d
+// (and n where d does not appear): sums along n and Xhat separately differ by O(1/|d|) from their
+// combination and lose that factor of precision for pixels close to the sample.
+//   acc[0] = sum g uX/Q (uX = u.Xhat)   acc[1] = sum g/Q   acc[2] = sum g A/(BQ)   acc[3] = sum g T
+//   acc[4..6]   = sum g eta d
+//   acc[7..9]   = sum g/Q (d + (A Qd/B^2) n)
+//   acc[10..12] = sum g/(BQ) (A d + Qd n)       (Qd = X'.d, Pd = Xdot.d)
+// FP64 version (the FP64 kernel and the FP32 kernel's near field)
 __device__ __forceinline__ void adj_pair64(double nx, double ny, double nz, double g, const Seg64 &s, int ngrad,
                                            double *acc, unsigned &zero)
 {
@@ -41,68 +49,71 @@ __device__ __forceinline__ void adj_pair64(double nx, double ny, double nz, doub
     const double B = 1.0 + (nx * s.xd[0] + ny * s.xd[1] + nz * s.xd[2]);
     const double Pd = s.xd[0] * dx + s.xd[1] * dy + s.xd[2] * dz;
     const double Qd = s.xp[0] * dx + s.xp[1] * dy + s.xp[2] * dz;
-    const double uX = (s.xd[0] * s.xh[0] + s.xd[1] * s.xh[1] + s.xd[2] * s.xh[2]) -
-                      (A / B) * (s.xp[0] * s.xh[0] + s.xp[1] * s.xh[1] + s.xp[2] * s.xh[2]);
     const double iQ = 1.0 / Q, iB = 1.0 / B;
     const double AB = A * iB;
-    const double ud = Pd - AB * Qd;
-    const double T = ud * iQ;
-    const double eta = 2.0 * T * iQ;
-    const double alpha = uX * iQ - eta;
+    const double uX = (s.xd[0] * s.xh[0] + s.xd[1] * s.xh[1] + s.xd[2] * s.xh[2]) -
+                      AB * (s.xp[0] * s.xh[0] + s.xp[1] * s.xh[1] + s.xp[2] * s.xh[2]);
+    const double T = (Pd - AB * Qd) * iQ;
     const double gq = g * iQ;
-    acc[0] += g * alpha;
+    acc[0] += gq * uX;
     acc[1] += gq;
     acc[2] += gq * AB;
     acc[3] += g * T;
-    const double ge = g * eta;
-    const double w2 = gq * (1.0 + AB * Qd * iB);
-    acc[4] += ge * nx;
-    acc[5] += ge * ny;
-    acc[6] += ge * nz;
-    acc[7] += w2 * nx;
-    acc[8] += w2 * ny;
-    acc[9] += w2 * nz;
+    const double ge = 2.0 * g * T * iQ;
+    acc[4] += ge * dx;
+    acc[5] += ge * dy;
+    acc[6] += ge * dz;
+    const double v = gq * AB * Qd * iB;
+    acc[7] += gq * dx + v * nx;
+    acc[8] += gq * dy + v * ny;
+    acc[9] += gq * dz + v * nz;
     if (ngrad == 9) {
-        const double w3 = gq * iB * (Qd + A);
-        acc[10] += w3 * nx;
-        acc[11] += w3 * ny;
-        acc[12] += w3 * nz;
+        const double gb = gq * iB;
+        const double ga = gb * A, gd = gb * Qd;
+        acc[10] += ga * dx + gd * nx;
+        acc[11] += ga * dy + gd * ny;
+        acc[12] += ga * dz + gd * nz;
     }
 }
 
-// FP32 pair derivative sums from the pair quantities (shared by the far and checked loops)
+// FP32 version from the pair quantities (shared by the far and checked loops); em1 = Xdot.Xhat,
+// f = X'.Xhat
 template <bool NG9>
-__device__ __forceinline__ void adj_pair32(float Q, float A, float B, float Pd, float Qd, float em1, float f,
-                                           float g, float nx, float ny, float nz, float *p)
+__device__ __forceinline__ void adj_pair32(float dx, float dy, float dz, float Q, float A, float B, float Pd,
+                                           float Qd, float em1, float f, float g, float nx, float ny, float nz,
+                                           float *p)
 {
     const float iQ = rcp_approx(Q), iB = rcp_approx(B);
     const float AB = A * iB;
-    const float ud = fmaf(-AB, Qd, Pd);
-    const float T = ud * iQ;
-    const float eta = 2.f * T * iQ;
-    const float alpha = fmaf(fmaf(-AB, f, em1), iQ, -eta);
+    const float T = fmaf(-AB, Qd, Pd) * iQ;
     const float gq = g * iQ;
-    p[0] = fmaf(g, alpha, p[0]);
+    p[0] = fmaf(gq, fmaf(-AB, f, em1), p[0]);
     p[1] += gq;
     p[2] = fmaf(gq, AB, p[2]);
     p[3] = fmaf(g, T, p[3]);
-    const float ge = g * eta;
-    const float w2 = gq * fmaf(AB * Qd, iB, 1.f);
-    p[4] = fmaf(ge, nx, p[4]);
-    p[5] = fmaf(ge, ny, p[5]);
-    p[6] = fmaf(ge, nz, p[6]);
-    p[7] = fmaf(w2, nx, p[7]);
-    p[8] = fmaf(w2, ny, p[8]);
-    p[9] = fmaf(w2, nz, p[9]);
+    const float ge = 2.f * (g * T) * iQ;
+    p[4] = fmaf(ge, dx, p[4]);
+    p[5] = fmaf(ge, dy, p[5]);
+    p[6] = fmaf(ge, dz, p[6]);
+    const float v = gq * (AB * Qd * iB);
+    p[7] = fmaf(gq, dx, fmaf(v, nx, p[7]));
+    p[8] = fmaf(gq, dy, fmaf(v, ny, p[8]));
+    p[9] = fmaf(gq, dz, fmaf(v, nz, p[9]));
     if (NG9) {
-        const float w3 = gq * iB * (Qd + A);
-        p[10] = fmaf(w3, nx, p[10]);
-        p[11] = fmaf(w3, ny, p[11]);
-        p[12] = fmaf(w3, nz, p[12]);
+        const float gb = gq * iB;
+        const float ga = gb * A, gd = gb * Qd;
+        p[10] = fmaf(ga, dx, fmaf(gd, nx, p[10]));
+        p[11] = fmaf(ga, dy, fmaf(gd, ny, p[11]));
+        p[12] = fmaf(ga, dz, fmaf(gd, nz, p[12]));
     }
 }
 
-// Gradient rows of one sample from its sums (FP64)
+// Gradient rows of one sample from its sums (FP64).  With c = -4 GU eps dsigma / |X| and
+// eps = sqrt(X'^2 / (1 - Xdot^2)):
+//   dTheta/dX     = (c/|X|) [eta d - (u - Xhat uX)/Q]    (c/|X| from dc/dX and the projection
+//                                                          of d(Xhat)/dX; the Xhat T terms cancel)
+//   dTheta/dXdot  = c [T Xdot / (1 - Xdot^2) + (d + (A Qd/B^2) n)/Q]
+//   dTheta/dX'    = c [T X' / X'^2 - (A d + Qd n)/(BQ)]
 __device__ __forceinline__ void adj_assemble(const Seg64 &s, const double *acc, int ngrad, double *out)
 {
     const double cX = s.c / s.X;
@@ -111,8 +122,8 @@ __device__ __forceinline__ void adj_assemble(const Seg64 &s, const double *acc, 
     for (int k = 0; k < 3; ++k) {
         const double xh = s.xh[k] + s.xl[k];
         out[k] = cX * (acc[0] * xh - acc[1] * s.xd[k] + acc[2] * s.xp[k] + acc[4 + k]);
-        out[3 + k] = s.c * (acc[3] / om2 * s.xd[k] - acc[1] * xh + acc[7 + k]);
-        if (ngrad == 9) out[6 + k] = s.c * ((xp2 > 0.0 ? acc[3] / xp2 : 0.0) * s.xp[k] + acc[2] * xh - acc[10 + k]);
+        out[3 + k] = s.c * (acc[3] / om2 * s.xd[k] + acc[7 + k]);
+        if (ngrad == 9) out[6 + k] = s.c * ((xp2 > 0.0 ? acc[3] / xp2 : 0.0) * s.xp[k] - acc[10 + k]);
     }
 }
 
@@ -200,14 +211,19 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
 #pragma unroll
                     for (int k = 0; k < kAcc; ++k) part[k] = 0.f;
                     if (far) {
+                        // derivatives scale as 1/Q^2: d is formed as a float pair even far away
 #pragma unroll 2
                         for (int q = w0; q < w0 + 32; ++q) {
-                            const float4 pa = sp[q].a;
-                            const float h = fmaf(-pa.z, r.a.z, fmaf(-pa.y, r.a.y, fmaf(-pa.x, r.a.x, 1.f)));
+                            const float4 pa = sp[q].a, pb = sp[q].b;
+                            const float dx = (pa.x - r.a.x) + (pb.x - r.b.x);
+                            const float dy = (pa.y - r.a.y) + (pb.y - r.b.y);
+                            const float dz = (pa.z - r.a.z) + (pb.z - r.b.z);
+                            const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                            const float Pd = fmaf(r.d.z, dz, fmaf(r.d.y, dy, r.d.x * dx));
+                            const float Qd = fmaf(r.e.z, dz, fmaf(r.e.y, dy, r.e.x * dx));
                             const float A = fmaf(pa.z, r.e.z, fmaf(pa.y, r.e.y, pa.x * r.e.x));
                             const float B = fmaf(pa.z, r.d.z, fmaf(pa.y, r.d.y, fmaf(pa.x, r.d.x, 1.f)));
-                            adj_pair32<NG9>(2.f * h, A, B, B - r.d.w, A - r.e.w, em1, r.e.w, pa.w, pa.x, pa.y, pa.z,
-                                            part);
+                            adj_pair32<NG9>(dx, dy, dz, Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
                         }
                     } else {
                         const float b_tiny = a.b_min * 1e-3f;
@@ -239,7 +255,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
                                     }
                                 }
                             } else {
-                                adj_pair32<NG9>(Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
+                                adj_pair32<NG9>(dx, dy, dz, Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
                             }
                         }
                     }
