@@ -73,6 +73,11 @@ def lib():
                                              _dp, ctypes.c_int64, ctypes.c_int64, _dp,
                                              ctypes.c_double, _dp, _dp, ctypes.c_int64, ctypes.c_int]
             L.or_isw_map_adjoint.restype = ctypes.c_int
+            L.or_lightcone_adjoint.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, ctypes.c_int64, _dp,
+                                               ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _dp, _dp,
+                                               _dp, ctypes.c_int64, ctypes.c_int, _dp, ctypes.c_int64, _dp,
+                                               ctypes.c_int64]
+            L.or_lightcone_adjoint.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -220,7 +225,8 @@ def isw_sum_dirs(dirs, samples, x_obs=(0.0, 0.0, 0.0), GU: float = 1.0):
 
 def isw_map_adjoint(nside: int, samples, g_pix, pix=None, x_obs=(0.0, 0.0, 0.0), GU: float = 1.0,
                     ngrad: int = 6, threads: int = 1):
-    """dL/d(X, Xdot[, X']) per sample for a per-pixel dL/dTheta: returns grad [ngrad, n]."""
+    """dL/d(X, Xdot[, X'[, dsigma]]) per sample for a per-pixel dL/dTheta: returns grad
+    [ngrad, n], ngrad in (6, 9, 10)."""
     samples = _c64(samples)
     n = samples.shape[1]
     if pix is None:
@@ -251,3 +257,28 @@ def isw_map_adjoint(nside: int, samples, g_pix, pix=None, x_obs=(0.0, 0.0, 0.0),
     if errors:
         raise ValueError(f"or_isw_map_adjoint failed with status {errors[0]}")
     return grad
+
+
+def lightcone_adjoint(mode: int, nodes, loop_params, tau, grad_samples, t_box: float = 0.0,
+                      x_obs=(0.0, 0.0, 0.0)):
+    """Chain dL/d(samples) (rows X, Xdot[, X'[, dsigma]]) through the light-cone solve.
+
+    Returns (grad_nodes [10, n], grad_loops [17, nloops] or None for LINEAR) and raises on a
+    non-OK status.  LINEAR: gradients of the box-time nodes (X, Xdot, X', dsigma).  BURDEN:
+    node rows 1 (sigma) and 9 (dsigma), and per-loop gradients of centre, rotation, L, psi, t0
+    (rows m, n stay zero)."""
+    nodes = _c64(nodes)
+    n = nodes.shape[1]
+    P = _c64(loop_params if loop_params is not None else np.zeros((17, 1)))
+    nloops = P.shape[1]
+    tau = _c64(tau)
+    gs = _c64(grad_samples)
+    assert gs.shape[1] == n and gs.shape[0] in (6, 9, 10)
+    gn = np.zeros((10, n))
+    gP = np.zeros((17, nloops)) if mode == BURDEN else None
+    st = lib().or_lightcone_adjoint(int(mode), _d(nodes), n, n, _d(P), nloops, nloops, float(t_box),
+                                    _d(_c64(x_obs)), _d(tau), _d(gs), n, gs.shape[0], _d(gn), n,
+                                    _d(gP) if gP is not None else None, nloops)
+    if st:
+        raise ValueError(f"or_lightcone_adjoint failed with status {st}")
+    return gn, gP

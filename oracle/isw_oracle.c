@@ -17,7 +17,9 @@
  *   3. retarded-time (past light cone) solve, LINEAR and BURDEN modes (Eq. 1: X cap x_gamma)
  *   4. per-segment weight eps*dsigma (text after Eq. 1) and the pair term of Eq. (1)-(2)
  *   5. the discrete line-of-sight sum per pixel, Neumaier-compensated, input order
- *   6. the analytic adjoint of the sum with respect to X and Xdot (and optionally X')
+ *   6. the analytic adjoint of the sum with respect to X and Xdot (optionally X', dsigma)
+ *   7. the adjoint of the light-cone solve (implicit-function theorem on the crossing
+ *      condition): gradients of LINEAR box-time nodes and of BURDEN loop parameters
  *
  * Pins (tests/test_oracle_*.py) tie each part to something other than itself; see the
  * header comment of each section for what pins it.
@@ -425,6 +427,7 @@ typedef struct {
     double X;            /* |X_s - x_obs| */
     double xd[3], xp[3]; /* Xdot, X' */
     double kappa;        /* -4 GU eps dsigma */
+    double kd;           /* -4 GU eps: kappa per unit dsigma */
     double om;           /* 1 - Xdot^2 */
     double xp2;          /* X'^2 */
     int ok;
@@ -446,6 +449,7 @@ static void seg_prepare(const double *samples, int64_t ld, int64_t s, const doub
     g->xp2 = (g->xp[0] * g->xp[0] + g->xp[1] * g->xp[1]) + g->xp[2] * g->xp[2];
     double eps = sqrt(g->xp2 / g->om);
     g->kappa = -4.0 * GU * (eps * dsig);
+    g->kd = -4.0 * GU * eps;
     g->ok = (g->om > 0.0) && (g->X > 0.0) && isfinite(g->kappa);
 }
 
@@ -558,8 +562,10 @@ int or_isw_sum_dirs(int64_t ndir, const double *dirs, int64_t ld_dir, const doub
  *   dt/dX_s    = kappa [ (h.n) Xhat - h ],  h = u/D^2 - 2 (u.D) D / D^4   (dD/dX_s = n Xhat^T - I)
  *   dt/dXdot   = t Xdot/(1 - Xdot^2) + kappa [ D + A (X'.D) n / B^2 ] / D^2
  *   dt/dX'     = t X'/X'^2 - kappa [ (X'.D) n + A D ] / (B D^2)
- * and dL/dq_s = sum_p g_p dt_ps/dq_s.  grad is double[ngrad][ldg] with rows X(3), Xdot(3)
- * and, when ngrad == 9, X'(3).  Pinned by central finite differences of the oracle map.
+ *   dt/ddsigma = t / dsigma = -4 GU eps (u.D)/D^2            (t is linear in dsigma)
+ * and dL/dq_s = sum_p g_p dt_ps/dq_s.  grad is double[ngrad][ldg] with rows X(3), Xdot(3),
+ * then X'(3) when ngrad >= 9 and dsigma when ngrad == 10.  Pinned by central finite
+ * differences of the oracle map and, for dsigma, by the linearity of the map in dsigma.
  * ---------------------------------------------------------------------------------- */
 int or_isw_map_adjoint(int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix,
                        const double *samples, int64_t n, int64_t ld, const double x_obs[3],
@@ -578,7 +584,7 @@ int or_isw_map_adjoint(int64_t nside, int64_t pix0, int64_t npix, const int64_t 
     for (int64_t s = 0; s < n; ++s) {
         seg_t g;
         seg_prepare(samples, ld, s, x_obs, GU, &g);
-        double acc[9] = {0}, cmp[9] = {0};
+        double acc[10] = {0}, cmp[10] = {0};
         for (int64_t k = 0; k < npix && g.ok; ++k) {
             const double *nv = nvs + 3 * k;
             pair_t q;
@@ -590,13 +596,14 @@ int or_isw_map_adjoint(int64_t nside, int64_t pix0, int64_t npix, const int64_t 
             for (int c = 0; c < 3; ++c) h[c] = q.u[c] * inv - 2.0 * q.uD * q.D[c] * inv * inv;
             double hn = (h[0] * nv[0] + h[1] * nv[1]) + h[2] * nv[2];
             double xhat[3] = {g.xh[0] + g.xl[0], g.xh[1] + g.xl[1], g.xh[2] + g.xl[2]};
-            double d[9];
+            double d[10];
             double B2 = q.B * q.B;
             for (int c = 0; c < 3; ++c) {
                 d[c] = g.kappa * (hn * xhat[c] - h[c]);
                 d[3 + c] = t * g.xd[c] / g.om + g.kappa * (q.D[c] + q.A * q.XpD * nv[c] / B2) * inv;
                 d[6 + c] = t * g.xp[c] / g.xp2 - g.kappa * (q.XpD * nv[c] + q.A * q.D[c]) / (q.B * q.D2);
             }
+            d[9] = g.kd * (q.uD / q.D2);
             for (int c = 0; c < ngrad; ++c) {
                 double tt = gp * d[c];
                 double x = acc[c] + tt;
@@ -609,4 +616,195 @@ int or_isw_map_adjoint(int64_t nside, int64_t pix0, int64_t npix, const int64_t 
     }
     free(nvs);
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------
+ * 7. Adjoint of the light-cone solve (an extension of the method: the derivative of the
+ * crossing condition X cap x_gamma of Eq. (1), with X', Xdot recorded at the crossing as in
+ * Sec. II.B).  A sample's X, Xdot, X' are the worldsheet at the retarded time tau, the root
+ * of F(tau) = |X(tau) - x_obs| - (t_obs - tau) = 0.  By the implicit-function theorem
+ *   dtau/dq = -(rhat . dX/dq|_t) / (1 + rhat . Xdot),   rhat = (X - x_obs) / |X - x_obs|,
+ * so with g_X, g_Xd, g_Xp = dL/d(sample X, Xdot, X') and the time derivatives of the three,
+ *   lambda = (g_X . dX/dt + g_Xd . dXdot/dt + g_Xp . dX'/dt) / (1 + rhat . Xdot),
+ *   gamma  = g_X - lambda rhat,
+ *   dL/dq  = gamma . dX/dq|_t + g_Xd . dXdot/dq|_t + g_Xp . dX'/dq|_t.
+ * LINEAR (straight worldline X = X_b + Xdot (tau - t_box); Xdot, X' constant):
+ *   dL/dX_b = gamma, dL/dXdot_b = g_Xd + (tau - t_box) gamma, dL/dX'_b = g_Xp,
+ *   dL/ddsigma_b = g_dsigma.
+ * BURDEN (X = c + R h, h = (a(u) + b(v))/2, u = sigma - (t - t0), v = sigma + (t - t0)):
+ *   dX/dt = R hd, hd = (b' - a')/2;  dXdot/dt = R hdd, hdd = (a'' + b'')/2;
+ *   dX'/dt = dXdot/dsigma = R hdp, hdp = (b'' - a'')/2;  dX/dsigma = X' = R hp, hp = (a' + b')/2,
+ *   dX'/dsigma = R hdd.  Per loop, summed over its samples in input order:
+ *   dL/dc = gamma;  dL/dR_kj = gamma_k h_j + g_Xd,k hd_j + g_Xp,k hp_j;
+ *   dL/dt0 = -(gamma . R hd + g_Xd . R hdd + g_Xp . R hdp)       (d/dt0 = -d/dt at fixed sigma);
+ *   dL/dL, dL/dpsi from da/dL = a/L - (u/L) a', da'/dL = -(u/L) a'' (b alike with v) and
+ *   db/dpsi, db'/dpsi.  Per sample: dL/dsigma = gamma . R hp + g_Xd . R hdp + g_Xp . R hdd
+ *   (node row 1) and dL/ddsigma (node row 9).  m and n are integer harmonic numbers: their
+ *   rows stay zero.  Pinned by central finite differences of the oracle's light-cone solve
+ *   followed by the oracle map.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+    double h[3], hd[3], hp[3], hdd[3], hdp[3];  /* h and its t / sigma derivatives */
+    double hL[3], hdL[3], hpL[3];               /* d/dL of h, hd, hp at fixed (sigma, t) */
+    double hs[3], hds[3], hps[3];               /* d/dpsi of h, hd, hp */
+} burden_jet_t;
+
+static void burden_jet(const double *P, int64_t ldp, int64_t id, double sigma, double t,
+                       burden_jet_t *J)
+{
+    const double two_pi = 2.0 * PI;
+    double L = P[12 * ldp + id], m = P[13 * ldp + id], n = P[14 * ldp + id];
+    double psi = P[15 * ldp + id], t0 = P[16 * ldp + id];
+    double dt = t - t0;
+    double u = sigma - dt, v = sigma + dt;
+    double sa, ca, sb, cb, sp, cp;
+    or_sincos_turns((m * u) / L, &sa, &ca);
+    or_sincos_turns((n * v) / L, &sb, &cb);
+    or_sincos_turns(psi / two_pi, &sp, &cp);
+    double ra = L / (two_pi * m), rb = L / (two_pi * n);
+    double ka = (two_pi * m) / L, kb = (two_pi * n) / L;
+    double a[3] = {ra * sa, -(ra * ca), 0.0};
+    double ap[3] = {ca, sa, 0.0};
+    double app[3] = {-(ka * sa), ka * ca, 0.0};
+    double b[3] = {rb * sb, -(rb * (cp * cb)), -(rb * (sp * cb))};
+    double bp[3] = {cb, cp * sb, sp * sb};
+    double bpp[3] = {-(kb * sb), kb * (cp * cb), kb * (sp * cb)};
+    double bs[3] = {0.0, rb * (sp * cb), -(rb * (cp * cb))};
+    double bps[3] = {0.0, -(sp * sb), cp * sb};
+    for (int k = 0; k < 3; ++k) {
+        double aL = a[k] / L - (u / L) * ap[k], bL = b[k] / L - (v / L) * bp[k];
+        double apL = -(u / L) * app[k], bpL = -(v / L) * bpp[k];
+        J->h[k] = 0.5 * (a[k] + b[k]);
+        J->hd[k] = 0.5 * (bp[k] - ap[k]);
+        J->hp[k] = 0.5 * (ap[k] + bp[k]);
+        J->hdd[k] = 0.5 * (app[k] + bpp[k]);
+        J->hdp[k] = 0.5 * (bpp[k] - app[k]);
+        J->hL[k] = 0.5 * (aL + bL);
+        J->hdL[k] = 0.5 * (bpL - apL);
+        J->hpL[k] = 0.5 * (apL + bpL);
+        J->hs[k] = 0.5 * bs[k];
+        J->hds[k] = 0.5 * bps[k];
+        J->hps[k] = 0.5 * bps[k];
+    }
+}
+
+static void mat_vec(const double R[9], const double x[3], double y[3])
+{
+    for (int k = 0; k < 3; ++k) y[k] = (R[3 * k] * x[0] + R[3 * k + 1] * x[1]) + R[3 * k + 2] * x[2];
+}
+
+static double dot3(const double *a, const double *b)
+{
+    return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+static void neumaier(double *acc, double *cmp, double t)
+{
+    double x = *acc + t;
+    if (fabs(*acc) >= fabs(t)) *cmp += (*acc - x) + t;
+    else *cmp += (t - x) + *acc;
+    *acc = x;
+}
+
+int or_lightcone_adjoint(int mode, const double *nodes, int64_t n, int64_t ld,
+                         const double *P, int64_t nloops, int64_t ldp, double t_box,
+                         const double x_obs[3], const double *tau, const double *gs, int64_t ldgs,
+                         int ngs, double *gn, int64_t ldgn, double *gP, int64_t ldgP)
+{
+    int worst = OR_OK;
+    double *cmp = NULL;
+    if (mode != 0) {
+        if (!gP) return OR_EINVAL;
+        cmp = (double *)calloc((size_t)(nloops > 0 ? nloops : 1) * 17, sizeof(double));
+        if (!cmp) return OR_EINVAL;
+        for (int r = 0; r < 17; ++r)
+            for (int64_t l = 0; l < nloops; ++l) gP[r * ldgP + l] = 0.0;
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        double gX[3], gXd[3], gXp[3] = {0.0, 0.0, 0.0}, gsig = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            gX[k] = gs[k * ldgs + s];
+            gXd[k] = gs[(3 + k) * ldgs + s];
+            if (ngs >= 9) gXp[k] = gs[(6 + k) * ldgs + s];
+        }
+        if (ngs >= 10) gsig = gs[9 * ldgs + s];
+        double out[10] = {0};
+        out[9] = gsig;
+        double t = tau[s];
+        if (mode == 0) {
+            double X[3], Xd[3], r[3];
+            double D = t - t_box;
+            for (int k = 0; k < 3; ++k) {
+                Xd[k] = nodes[(3 + k) * ld + s];
+                X[k] = nodes[k * ld + s] + Xd[k] * D;
+                r[k] = X[k] - x_obs[k];
+            }
+            double rn = sqrt(dot3(r, r));
+            double den = 1.0 + dot3(r, Xd) / rn;
+            if (!(rn > 0.0) || !(den > 0.0)) {
+                worst = OR_EDOMAIN > worst ? OR_EDOMAIN : worst;
+            } else {
+                double lam = dot3(gX, Xd) / den;
+                for (int k = 0; k < 3; ++k) {
+                    double gam = gX[k] - lam * (r[k] / rn);
+                    out[k] = gam;
+                    out[3 + k] = gXd[k] + D * gam;
+                    out[6 + k] = gXp[k];
+                }
+            }
+        } else {
+            int64_t id = (int64_t)nodes[s];
+            double sigma = nodes[ld + s];
+            if (id < 0 || id >= nloops) {
+                worst = OR_EINVAL > worst ? OR_EINVAL : worst;
+            } else {
+                double R[9], c[3];
+                for (int k = 0; k < 3; ++k) c[k] = P[k * ldp + id];
+                for (int k = 0; k < 9; ++k) R[k] = P[(3 + k) * ldp + id];
+                burden_jet_t J;
+                burden_jet(P, ldp, id, sigma, t, &J);
+                double Rh[3], Xd[3], Xp[3], Xdd[3], Xdp[3], r[3];
+                mat_vec(R, J.h, Rh);
+                mat_vec(R, J.hd, Xd);
+                mat_vec(R, J.hp, Xp);
+                mat_vec(R, J.hdd, Xdd);
+                mat_vec(R, J.hdp, Xdp);
+                for (int k = 0; k < 3; ++k) r[k] = (c[k] + Rh[k]) - x_obs[k];
+                double rn = sqrt(dot3(r, r));
+                double den = 1.0 + dot3(r, Xd) / rn;
+                if (!(rn > 0.0) || !(den > 0.0)) {
+                    worst = OR_EDOMAIN > worst ? OR_EDOMAIN : worst;
+                } else {
+                    double lam = (dot3(gX, Xd) + dot3(gXd, Xdd) + dot3(gXp, Xdp)) / den;
+                    double gam[3];
+                    for (int k = 0; k < 3; ++k) gam[k] = gX[k] - lam * (r[k] / rn);
+                    out[1] = (dot3(gam, Xp) + dot3(gXd, Xdp)) + dot3(gXp, Xdd);
+                    double contrib[17] = {0};
+                    for (int k = 0; k < 3; ++k) contrib[k] = gam[k];
+                    for (int k = 0; k < 3; ++k)
+                        for (int j = 0; j < 3; ++j)
+                            contrib[3 + 3 * k + j] = (gam[k] * J.h[j] + gXd[k] * J.hd[j]) + gXp[k] * J.hp[j];
+                    double v1[3], v2[3], v3[3];
+                    mat_vec(R, J.hL, v1);
+                    mat_vec(R, J.hdL, v2);
+                    mat_vec(R, J.hpL, v3);
+                    contrib[12] = (dot3(gam, v1) + dot3(gXd, v2)) + dot3(gXp, v3);
+                    mat_vec(R, J.hs, v1);
+                    mat_vec(R, J.hds, v2);
+                    mat_vec(R, J.hps, v3);
+                    contrib[15] = (dot3(gam, v1) + dot3(gXd, v2)) + dot3(gXp, v3);
+                    contrib[16] = -((dot3(gam, Xd) + dot3(gXd, Xdd)) + dot3(gXp, Xdp));
+                    for (int q = 0; q < 17; ++q)
+                        neumaier(&gP[q * ldgP + id], &cmp[q * nloops + id], contrib[q]);
+                }
+            }
+        }
+        for (int q = 0; q < 10; ++q) gn[q * ldgn + s] = out[q];
+    }
+    if (cmp) {
+        for (int q = 0; q < 17; ++q)
+            for (int64_t l = 0; l < nloops; ++l) gP[q * ldgP + l] += cmp[q * nloops + l];
+        free(cmp);
+    }
+    return worst;
 }
