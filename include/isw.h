@@ -161,12 +161,40 @@ int isw_map(isw_ctx *ctx, int64_t nside, int64_t pix0, int64_t npix, const int64
 
 /* Adjoint of isw_map with respect to the samples (an extension of the method: the
  * derivative of Eq. (1)-(2)).  Given g = dL/dTheta (device double[npix], same pixel
- * selection), writes grad_out = device double[ngrad][ld_g] with rows dL/dX (3), dL/dXdot (3)
- * and, when ngrad = 9, dL/dX' (3), for every sample (dsigma held fixed).  Pair terms are
- * recomputed, not stored; the reduction over pixels has a fixed order (deterministic). */
+ * selection), writes grad_out = device double[ngrad][ld_g] with rows dL/dX (3), dL/dXdot (3),
+ * then dL/dX' (3) when ngrad >= 9 and dL/ddsigma when ngrad = 10 (ngrad is 6, 9 or 10), for
+ * every sample.  Pair terms are recomputed, not stored; the reduction over pixels has a fixed
+ * order (deterministic).  A skipped sample (|Xdot| >= 1) gets zero rows. */
 int isw_map_adjoint(isw_ctx *ctx, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list,
                     const double *samples, int64_t n, int64_t ld, const double *x_obs, double GU, int prec,
                     const double *dL_dtheta, double *grad_out, int64_t ld_g, int ngrad, void *stream);
+
+/* Adjoint of lightcone_intersect (an extension of the method: the derivative of the crossing
+ * condition X cap x_gamma of Eq. (1), with X', Xdot taken at the crossing as in Sec. II.B).
+ * The retarded time tau solves |X(tau) - x_obs| = t_obs - tau, so by the implicit-function
+ * theorem dtau/dq = -(rhat . dX/dq) / (1 + rhat . Xdot) for every parameter q of the node.
+ *   mode, nodes_in, n, ld, loop_params, nloops, ldp, t_box, x_obs : as given to
+ *              lightcone_intersect (x_obs host double[3], NULL = origin)
+ *   tau      : device double[n], the tau_out of that call
+ *   grad_samples : device double[ngrad][ld_gs], dL/d(samples): rows X (3), Xdot (3), then
+ *              X' (3) and dsigma when ngrad is 9 or 10 (the rows isw_map_adjoint writes);
+ *              rows not given count as zero
+ *   grad_nodes : device double[10][ld_gn].  LINEAR: dL/d(box-time X, Xdot, X', dsigma).
+ *              BURDEN: row 1 = dL/dsigma, row 9 = dL/ddsigma, other rows 0.
+ *   grad_loops : BURDEN only (ignored for LINEAR, may be NULL): device double[17][ld_gl],
+ *              ld_gl >= nloops: dL/d(centre (3), rotation (9 entries, each taken as a free
+ *              parameter), L, m, n, psi, t0) summed over the loop's nodes; the m and n rows are
+ *              0 (integer harmonic numbers).  The nodes of one loop must be contiguous in
+ *              nodes_in: a loop whose nodes form several runs gets NaN rows and ISW_EINVAL in
+ *              the device status.  The per-loop sum has a fixed order (deterministic).
+ * A node with an out-of-range loop id gets zero rows (ISW_EINVAL in the device status); one
+ * where 1 + rhat . Xdot <= 0 gets zero rows (ISW_EDOMAIN).  ISW_EINVAL on the host for bad
+ * sizes, modes or pointers. */
+int lightcone_adjoint(isw_ctx *ctx, int mode, const double *nodes_in, int64_t n, int64_t ld,
+                      const double *loop_params, int64_t nloops, int64_t ldp, double t_box,
+                      const double *x_obs, const double *tau, const double *grad_samples, int64_t ld_gs,
+                      int ngrad, double *grad_nodes, int64_t ld_gn, double *grad_loops, int64_t ld_gl,
+                      void *stream);
 
 /* Many shells into one full-sky map (Sec. III.A: the final map is the sum of maps sourced
  * by subsets of the simulation cones).  nodes: device double[10][ld] of all shells

@@ -76,6 +76,8 @@ def lib():
                                            _vp, _i64, _i32, _vp]),
                 "isw_map_batched": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp,
                                            _dbl, _dbl, _i32, _i32, _i32, _vp, _vp]),
+                "lightcone_adjoint": (_i32, [_vp, _i32, _vp, _i64, _i64, _vp, _i64, _i64, _dbl, _vp, _vp, _vp,
+                                             _i64, _i32, _vp, _i64, _vp, _i64, _vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -269,7 +271,8 @@ def isw_map(nside: int, samples, pix=None, pix0: int = 0, npix: int | None = Non
 
 def isw_map_adjoint(nside: int, samples, dL_dtheta, pix=None, pix0: int = 0, npix: int | None = None, x_obs=None,
                     GU: float = 1.0, prec="f32c", ngrad: int = 6, out=None, ctx=None, stream=None):
-    """dL/dX, dL/dXdot (and dL/dX' when ngrad = 9) per sample: float64 CUDA tensor [ngrad, n]."""
+    """dL/dX, dL/dXdot (then dL/dX' when ngrad >= 9 and dL/ddsigma when ngrad = 10) per sample:
+    float64 CUDA tensor [ngrad, n]."""
     c = _ctx(ctx)
     _dev_tensor(samples, torch.float64, "samples")
     n, ld = _rows(samples, 10, "samples")
@@ -278,8 +281,8 @@ def isw_map_adjoint(nside: int, samples, dL_dtheta, pix=None, pix0: int = 0, npi
     g = dL_dtheta.contiguous()
     if g.numel() != npix:
         raise ValueError("dL_dtheta must have one value per selected pixel")
-    if ngrad not in (6, 9):
-        raise ValueError("ngrad must be 6 or 9")
+    if ngrad not in (6, 9, 10):
+        raise ValueError("ngrad must be 6, 9 or 10")
     if out is None:
         out = torch.empty((ngrad, n), dtype=torch.float64, device=samples.device)
     _dev_tensor(out, torch.float64, "out")
@@ -321,9 +324,51 @@ def isw_map_batched(nside: int, nodes, shell_off, t_box, mode, loop_params=None,
     return out
 
 
+def lightcone_adjoint(mode: int, nodes, tau, grad_samples, loop_params=None, t_box: float = 0.0, x_obs=None,
+                      out=None, out_loops=None, ctx=None, stream=None):
+    """Chain dL/d(samples) (rows X, Xdot[, X'[, dsigma]], e.g. from isw_map_adjoint) through the
+    light-cone solve.  Returns (grad_nodes [10, n], grad_loops [17, nloops] or None for LINEAR):
+    LINEAR gives the box-time node gradients; BURDEN gives node rows 1 (sigma) and 9 (dsigma) and
+    the per-loop parameter gradients (the nodes of one loop must be contiguous)."""
+    c = _ctx(ctx)
+    _dev_tensor(nodes, torch.float64, "nodes")
+    n, ld = _rows(nodes, 10, "nodes")
+    _dev_tensor(tau, torch.float64, "tau")
+    if tau.numel() != n or not tau.is_contiguous():
+        raise ValueError("tau must be a contiguous float64 tensor of n elements")
+    _dev_tensor(grad_samples, torch.float64, "grad_samples")
+    ngrad = grad_samples.shape[0]
+    if ngrad not in (6, 9, 10):
+        raise ValueError("grad_samples must have 6, 9 or 10 rows")
+    n2, ld_gs = _rows(grad_samples, ngrad, "grad_samples")
+    if n2 != n:
+        raise ValueError("grad_samples must have as many columns as nodes")
+    if out is None:
+        out = torch.empty((10, n), dtype=torch.float64, device=nodes.device)
+    _dev_tensor(out, torch.float64, "out")
+    _, ld_gn = _rows(out, 10, "out")
+    P, nloops, ldp, ld_gl = None, 0, 0, 0
+    if mode == BURDEN:
+        if loop_params is None:
+            raise ValueError("BURDEN mode needs loop_params")
+        _dev_tensor(loop_params, torch.float64, "loop_params")
+        nloops, ldp = _rows(loop_params, 17, "loop_params")
+        P = loop_params
+        if out_loops is None:
+            out_loops = torch.empty((17, nloops), dtype=torch.float64, device=nodes.device)
+        _dev_tensor(out_loops, torch.float64, "out_loops")
+        _, ld_gl = _rows(out_loops, 17, "out_loops")
+    else:
+        out_loops = None
+    c.check(lib().lightcone_adjoint(c.handle, int(mode), _ptr(nodes), n, ld, _ptr(P), nloops, ldp, float(t_box),
+                                    _xobs(x_obs), _ptr(tau), _ptr(grad_samples), ld_gs, int(ngrad), _ptr(out), ld_gn,
+                                    _ptr(out_loops), ld_gl, _stream(stream)))
+    return out, out_loops
+
+
 class ISWMap(torch.autograd.Function):
-    """Theta = isw_map(samples); backward returns dL/dsamples with rows X, Xdot (and X' if
-    ``ngrad`` = 9) from isw_map_adjoint; the dsigma row gets no gradient."""
+    """Theta = isw_map(samples); backward returns dL/dsamples with rows X, Xdot, then X' if
+    ``ngrad`` >= 9 and dsigma if ``ngrad`` = 10, from isw_map_adjoint (other rows zero)."""
 
     @staticmethod
     def forward(ctx, samples, nside, pix=None, x_obs=None, GU=1.0, prec="f32c", ngrad=6):
@@ -340,3 +385,32 @@ class ISWMap(torch.autograd.Function):
         grad = torch.zeros_like(samples)
         grad[:ngrad] = g
         return grad, None, None, None, None, None, None
+
+
+class ISWLightconeMap(torch.autograd.Function):
+    """Theta = isw_map(lightcone_intersect(nodes)) differentiable end to end.
+
+    LINEAR: ``apply(nodes, None, nside, LINEAR, t_box, ...)`` with gradients for the box-time
+    nodes (X, Xdot, X', dsigma).  BURDEN: ``apply(nodes, loop_params, nside, BURDEN, ...)`` with
+    gradients for node rows sigma and dsigma and for the loop parameters.  Backward runs
+    isw_map_adjoint (all 10 sample rows) and lightcone_adjoint on the GPU."""
+
+    @staticmethod
+    def forward(ctx, nodes, loop_params, nside, mode, t_box=0.0, pix=None, x_obs=None, t_obs=1.0, GU=1.0,
+                prec="f32c"):
+        n = nodes.shape[1]
+        tau = torch.empty(n, dtype=torch.float64, device=nodes.device)
+        P = loop_params.detach() if loop_params is not None else None
+        samples = lightcone_intersect(mode, nodes.detach(), P, t_box=t_box, x_obs=x_obs, t_obs=t_obs, tau=tau)
+        ctx.save_for_backward(nodes, P, samples, tau, pix)
+        ctx.args = (nside, mode, t_box, x_obs, GU, prec, loop_params is not None)
+        return isw_map(nside, samples, pix=pix, x_obs=x_obs, GU=GU, prec=prec)
+
+    @staticmethod
+    def backward(ctx, grad_theta):
+        nodes, P, samples, tau, pix = ctx.saved_tensors
+        nside, mode, t_box, x_obs, GU, prec, has_loops = ctx.args
+        gs = isw_map_adjoint(nside, samples, grad_theta.contiguous().to(torch.float64), pix=pix, x_obs=x_obs, GU=GU,
+                             prec=prec, ngrad=10)
+        gn, gl = lightcone_adjoint(mode, nodes.detach(), tau, gs, loop_params=P, t_box=t_box, x_obs=x_obs)
+        return gn, (gl if has_loops else None), None, None, None, None, None, None, None, None

@@ -67,7 +67,7 @@ __device__ __forceinline__ void adj_pair64(double nx, double ny, double nz, doub
     acc[7] += gq * dx + v * nx;
     acc[8] += gq * dy + v * ny;
     acc[9] += gq * dz + v * nz;
-    if (ngrad == 9) {
+    if (ngrad >= 9) {
         const double gb = gq * iB;
         const double ga = gb * A, gd = gb * Qd;
         acc[10] += ga * dx + gd * nx;
@@ -114,6 +114,8 @@ __device__ __forceinline__ void adj_pair32(float dx, float dy, float dz, float Q
 //                                                          of d(Xhat)/dX; the Xhat T terms cancel)
 //   dTheta/dXdot  = c [T Xdot / (1 - Xdot^2) + (d + (A Qd/B^2) n)/Q]
 //   dTheta/dX'    = c [T X' / X'^2 - (A d + Qd n)/(BQ)]
+//   dTheta/ddsigma = (c / dsigma) T = cu T                  (the term is linear in dsigma)
+// Rows: X (3), Xdot (3), then X' (3) when ngrad >= 9 and dsigma when ngrad == 10.
 __device__ __forceinline__ void adj_assemble(const Seg64 &s, const double *acc, int ngrad, double *out)
 {
     const double cX = s.c / s.X;
@@ -123,8 +125,9 @@ __device__ __forceinline__ void adj_assemble(const Seg64 &s, const double *acc, 
         const double xh = s.xh[k] + s.xl[k];
         out[k] = cX * (acc[0] * xh - acc[1] * s.xd[k] + acc[2] * s.xp[k] + acc[4 + k]);
         out[3 + k] = s.c * (acc[3] / om2 * s.xd[k] + acc[7 + k]);
-        if (ngrad == 9) out[6 + k] = s.c * ((xp2 > 0.0 ? acc[3] / xp2 : 0.0) * s.xp[k] - acc[10 + k]);
+        if (ngrad >= 9) out[6 + k] = s.c * ((xp2 > 0.0 ? acc[3] / xp2 : 0.0) * s.xp[k] - acc[10 + k]);
     }
+    if (ngrad == 10) out[9] = s.cu * acc[3];
 }
 
 __global__ void k_pack_pixels(const double *__restrict__ nv, int64_t ldn, const int64_t *__restrict__ outidx,
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
         s_abort = 0;
     }
     __syncthreads();
-    constexpr int NG = NG9 ? 9 : 6;
+    const int NG = a.ngrad;   // 6, or 9 / 10 with NG9
     unsigned nearcnt = 0, zerocnt = 0;
     uint32_t gl = 0;
     const int64_t n_items = a.nseg_tiles * a.split;
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
         gl += nt;
         if (s < a.n) {
             const Seg64 s64 = a.s64[s];
-            double acc[kAcc], out[9];
+            double acc[kAcc], out[10];
 #pragma unroll
             for (int k = 0; k < kAcc; ++k) acc[k] = (double)ahi[k] + (double)alo[k];
             adj_assemble(s64, acc, NG, out);
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(NT) k_adj_f64(AdjArgs a)
         }
         gl += nt;
         if (s < a.n) {
-            double out[9];
+            double out[10];
             adj_assemble(s64, acc, NG, out);
             if (a.split == 1) {
                 for (int k = 0; k < NG; ++k) a.grad[k * a.ld_g + s] = out[k];
@@ -401,7 +404,7 @@ int adj_slots(int prec, int ngrad, int num_sms)
 {
     int nb = 0;
     if (prec == ISW_F32C) {
-        const void *fn = ngrad == 9 ? (const void *)&k_adj_f32c<kAdjNT, kAdjTP, true>
+        const void *fn = ngrad >= 9 ? (const void *)&k_adj_f32c<kAdjNT, kAdjTP, true>
                                     : (const void *)&k_adj_f32c<kAdjNT, kAdjTP, false>;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kAdjNT, smem_adj32());
     } else {
@@ -424,7 +427,7 @@ void launch_adjoint(int prec, const AdjArgs &a, int grid, cudaStream_t s)
 {
     void *args[] = {(void *)&a};
     if (prec == ISW_F32C) {
-        const void *fn = a.ngrad == 9 ? (const void *)&k_adj_f32c<kAdjNT, kAdjTP, true>
+        const void *fn = a.ngrad >= 9 ? (const void *)&k_adj_f32c<kAdjNT, kAdjTP, true>
                                       : (const void *)&k_adj_f32c<kAdjNT, kAdjTP, false>;
         cudaLaunchKernel(fn, dim3(grid), dim3(kAdjNT), args, smem_adj32(), s);
     } else {

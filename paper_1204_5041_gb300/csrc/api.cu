@@ -14,7 +14,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsCount
 };
 
 int set_err(isw_ctx *c, int code, const char *fmt, ...)
@@ -476,6 +476,49 @@ int lightcone_intersect(isw_ctx *c, int mode, const double *nodes_in, int64_t n,
     return check_launch(c, "lightcone_intersect launch");
 }
 
+int lightcone_adjoint(isw_ctx *c, int mode, const double *nodes_in, int64_t n, int64_t ld, const double *loop_params,
+                      int64_t nloops, int64_t ldp, double t_box, const double *x_obs, const double *tau,
+                      const double *grad_samples, int64_t ld_gs, int ngrad, double *grad_nodes, int64_t ld_gn,
+                      double *grad_loops, int64_t ld_gl, void *stream)
+{
+    if (!c) return ISW_EINVAL;
+    if (mode != ISW_LINEAR && mode != ISW_BURDEN) return set_err(c, ISW_EINVAL, "unknown mode %d", mode);
+    int r;
+    if ((r = check_samples(c, nodes_in, n, ld))) return r;
+    if (ngrad != 6 && ngrad != 9 && ngrad != 10) return set_err(c, ISW_EINVAL, "ngrad must be 6, 9 or 10");
+    if (mode == ISW_BURDEN) {
+        if (nloops <= 0 || ldp < nloops || !is_device_ptr(loop_params))
+            return set_err(c, ISW_EINVAL, "BURDEN mode needs device loop_params[17][ldp], ldp >= nloops > 0");
+        if (ld_gl < nloops || !is_device_ptr(grad_loops))
+            return set_err(c, ISW_EINVAL, "BURDEN mode needs device grad_loops[17][ld_gl], ld_gl >= nloops");
+    }
+    if (n > 0) {
+        if (ld_gs < n || ld_gn < n) return set_err(c, ISW_EINVAL, "ld_gs and ld_gn must be >= n");
+        if (!is_device_ptr(tau) || !is_device_ptr(grad_samples) || !is_device_ptr(grad_nodes))
+            return set_err(c, ISW_EINVAL, "tau, grad_samples and grad_nodes must be device pointers");
+    }
+    if (mode == ISW_LINEAR && !std::isfinite(t_box)) return set_err(c, ISW_EINVAL, "t_box not finite");
+    if ((r = set_device(c))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *runs = nullptr;
+    int64_t *first = nullptr, *last = nullptr;
+    if (mode == ISW_BURDEN) {
+        const size_t nl = (size_t)nloops;
+        if ((r = ensure_ws(c, kWsLoops, nl * (2 * sizeof(int64_t) + sizeof(int)) + 16))) return r;
+        first = (int64_t *)c->ws[kWsLoops];
+        last = first + nl;
+        runs = (int *)(last + nl);
+        cudaError_t e = cudaMemsetAsync(runs, 0, nl * sizeof(int), s);
+        if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync");
+    }
+    const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
+    launch_lightcone_adjoint(mode, nodes_in, n, ld, loop_params, nloops, ldp, t_box, xo[0], xo[1], xo[2], tau,
+                             grad_samples, ld_gs, ngrad, grad_nodes, ld_gn, grad_loops, ld_gl, runs, first, last,
+                             c->d_status, s);
+    c->n_launch += (n > 0 ? 1 : 0) + (mode == ISW_BURDEN ? 1 : 0);
+    return check_launch(c, "lightcone_adjoint launch");
+}
+
 int isw_map(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list, const double *samples,
             int64_t n, int64_t ld, const double *x_obs, double GU, int prec, int accumulate, double *theta_out,
             void *stream)
@@ -501,7 +544,7 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     if ((r = check_pixels(c, nside, pix0, npix, pix_list))) return r;
     if ((r = check_samples(c, samples, n, ld))) return r;
     if (prec != ISW_F64 && prec != ISW_F32C) return set_err(c, ISW_EINVAL, "unknown precision %d", prec);
-    if (ngrad != 6 && ngrad != 9) return set_err(c, ISW_EINVAL, "ngrad must be 6 or 9");
+    if (ngrad != 6 && ngrad != 9 && ngrad != 10) return set_err(c, ISW_EINVAL, "ngrad must be 6, 9 or 10");
     if (n == 0) return ISW_OK;
     if (ld_g < n) return set_err(c, ISW_EINVAL, "ld_g < n");
     if (!is_device_ptr(grad_out)) return set_err(c, ISW_EINVAL, "grad_out is not a device pointer");

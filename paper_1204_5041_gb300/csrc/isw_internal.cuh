@@ -270,7 +270,8 @@ struct DevStatus {
 // radius, e = 1 + Xdot.Xhat, f = X'.Xhat (so that Xdot.d = B - e and X'.d = A - f for
 // d = n - Xhat); the last four give B = (1 - |Xdot|) + |Xdot| |n + Xdot/|Xdot||^2 / 2
 // without cancellation when n approaches -Xdot/|Xdot|.
-// FP64 record (128 B): Xhat hi (3), Xhat lo (3), Xdot (3), X' (3), c, 1 - |Xdot|, |X - x_obs|, 0.
+// FP64 record (128 B): Xhat hi (3), Xhat lo (3), Xdot (3), X' (3), c, 1 - |Xdot|, |X - x_obs|,
+// cu = c / dsigma = -4 GU eps / |X| (the weight per unit dsigma, for the dsigma gradient).
 // Segment tile cap (48 B): centre (3), chord radius, max rho, min (1 - |Xdot|), beam cap (4).
 // Pixel tile cap (16 B): centre (3), chord radius.
 // ------------------------------------------------------------------------------------
@@ -286,7 +287,7 @@ struct __align__(16) Far32 {
     float4 a, b, c, d;
 };
 struct __align__(16) Seg64 {
-    double xh[3], xl[3], xd[3], xp[3], c, om, X, pad1;   // X = |X_s - x_obs|
+    double xh[3], xl[3], xd[3], xp[3], c, om, X, cu;   // X = |X_s - x_obs|
 };
 // Pixel records of the adjoint: FP32 (n hi, g | n lo, 0) and FP64 (n, g); padding slots
 // hold n = 0, g = 0 so that every pair stays finite and contributes nothing.

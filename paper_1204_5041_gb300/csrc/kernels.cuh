@@ -23,6 +23,13 @@ void launch_lightcone_shells(const double *nodes, int64_t n, int64_t ld, const i
                              double xo0, double xo1, double xo2, double t_obs, double tol, double *out,
                              int64_t ld_out, DevStatus *st, cudaStream_t s);
 
+// lcadj.cu: adjoint of the light-cone solve.  runs (int[nloops], zeroed by the caller), first,
+// last (int64[nloops]) are workspace of the Burden per-loop reduction; gl may be NULL in LINEAR mode.
+void launch_lightcone_adjoint(int mode, const double *nodes, int64_t n, int64_t ld, const double *P, int64_t nloops,
+                              int64_t ldp, double t_box, double xo0, double xo1, double xo2, const double *tau,
+                              const double *gs, int64_t ldgs, int ngs, double *gn, int64_t ldgn, double *gl,
+                              int64_t ldgl, int *runs, int64_t *first, int64_t *last, DevStatus *st, cudaStream_t s);
+
 // pack.cu: per-sample records of the map kernels and per-tile caps
 // far (may be NULL): far-field records for the FP32 pair kernel
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,

@@ -85,6 +85,7 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
                 ++bad;
             }
             g.c = c;
+            g.cu = ok ? ddiv(dmul(-4.0 * GU, eps), X) : 0.0;
             g.om = ok ? dsub(1.0, dsqrt(v2)) : 1.0;
             g.X = ok ? X : 1.0;
             // near-field chord radius: near_k * max(pixel size, angular length of the segment)
@@ -122,11 +123,13 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
                 for (int k = 0; k < 3; ++k) g.xh[k] = g.xl[k] = g.xd[k] = g.xp[k] = 0.0;
                 g.om = 1.0;
                 g.X = 1.0;
+                g.cu = 0.0;
             }
         } else {
             // padding: zero weight at Xhat = 0 (so d = n, d.d = 1), never near, B = 1
             for (int k = 0; k < 3; ++k) g.xh[k] = g.xl[k] = g.xd[k] = g.xp[k] = 0.0;
             g.c = 0.0;
+            g.cu = 0.0;
             g.om = 1.0;
             g.X = 1.0;
             f.a = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -135,7 +138,6 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
             f.e = make_float4(0.f, 0.f, 0.f, 0.f);
             f.k = make_float4(0.f, 0.f, 0.f, 1.f);
         }
-        g.pad1 = 0.0;
         s32[s] = f;
         s64[s] = g;
         if (far) {
