@@ -14,7 +14,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsCount
 };
 
 int set_err(isw_ctx *c, int code, const char *fmt, ...)
@@ -212,8 +212,9 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     if ((r = ensure_ws(c, kWsS32, (size_t)n_pad * sizeof(Seg32)))) return r;
     if ((r = ensure_ws(c, kWsS64, (size_t)n_pad * sizeof(Seg64)))) return r;
     if ((r = ensure_ws(c, kWsScap, (size_t)nst * sizeof(SegCap)))) return r;
-    if (prec == ISW_F32C && (r = ensure_ws(c, kWsFar, (size_t)n_pad * sizeof(Far32)))) return r;
+    if (prec == ISW_F32C && (r = ensure_ws(c, kWsFar, (size_t)(n_pad / 2) * sizeof(Far2)))) return r;
     if (split > 1 && (r = ensure_ws(c, kWsPartial, (size_t)split * pp.tot * sizeof(double)))) return r;
+    if (prec == ISW_F32C && (r = ensure_ws(c, kWsQueue, 2 * sizeof(unsigned long long)))) return r;
 
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     double *nv = (double *)c->ws[kWsNv];
@@ -225,7 +226,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
 
     launch_pixel_table(nside, pp.mode, pix0, npix, pix_list, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx, pcaps,
                        c->d_status, s);
-    Far32 *far = prec == ISW_F32C ? (Far32 *)c->ws[kWsFar] : nullptr;
+    Far2 *far = prec == ISW_F32C ? (Far2 *)c->ws[kWsFar] : nullptr;
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, far, c->d_status, s);
     c->n_launch += 3;
     if (prec == ISW_F32C) {
@@ -251,6 +252,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.partial = split > 1 ? (double *)c->ws[kWsPartial] : nullptr;
     a.accumulate = accumulate;
     a.st = c->d_status;
+    a.queue = prec == ISW_F32C ? (unsigned long long *)c->ws[kWsQueue] : nullptr;
     // timing a variant: every k-th pixel tile (all its segment chunks), about tune_waves waves
     a.tile_stride = 1;
     if (tune_waves > 0) {
@@ -263,6 +265,8 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     // the timed pair work: far pass (or the FP64 kernel), chunk reduce, near-field pass
     const int ti = timing_begin(c, s);
     if (prec == ISW_F32C) {
+        cudaError_t e = cudaMemsetAsync(a.queue, 0, 2 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync(work counters)");
         launch_map_f32c(vidx, a, grid, s);
         // near-field pass: adds the segment tiles the far pass skipped, chunk by chunk
         launch_map_f32c_near(vidx, a, c->num_sms, s);

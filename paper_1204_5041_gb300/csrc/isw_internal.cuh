@@ -278,14 +278,56 @@ struct DevStatus {
 struct __align__(16) Seg32 {
     float4 a, b, d, e, k;
 };
-// Far-field record (64 B) with sigma = sign(c), s = sqrt(|c|/2):
-//   a = (-sigma Xhat, sigma), b = (Xdot, -s e/2), c = (s X', -s f/2), d = (s, K, 0, 0),
+// Far-field constants of one sample, with sigma = sign(c), s = sqrt(|c|/2):
+//   a = (-sigma Xhat, sigma), b = (Xdot, -s e/2), c = (s X', -s f/2), d = (s, K),
 //   K = (|c|/2) (f^2 - e^2)/4, so that for |d| >= d_far the pair term is
 //   t = [(s B - s e/2)^2 - (s A - s f/2)^2 + K] / [B sigma (1 - n.Xhat)]   (completed squares of
 //   c/2 [B (B - e) - A (A - f)] / [B (1 - n.Xhat)]).
-struct __align__(16) Far32 {
-    float4 a, b, c, d;
+// The far pass stores them for samples 2i and 2i+1 interleaved (112 B per pair): the 14
+// constants (a.xyzw, b.xyzw, c.xyzw, d.x, d.y) in that order, each as a float pair (sample 2i,
+// sample 2i+1), so that one packed f32x2 instruction serves both samples.
+struct __align__(16) Far2 {
+    float4 v[7];
 };
+constexpr int kFarConsts = 14;
+
+// Packed FP32 pairs (f32x2, sm_100 and later): two IEEE single operations per instruction,
+// round to nearest; a 64-bit register holds (lo, hi).
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 struct __align__(16) Seg64 {
     double xh[3], xl[3], xd[3], xp[3], c, om, X, cu;   // X = |X_s - x_obs|
 };

@@ -31,9 +31,9 @@ void launch_lightcone_adjoint(int mode, const double *nodes, int64_t n, int64_t 
                               int64_t ldgl, int *runs, int64_t *first, int64_t *last, DevStatus *st, cudaStream_t s);
 
 // pack.cu: per-sample records of the map kernels and per-tile caps
-// far (may be NULL): far-field records for the FP32 pair kernel
+// far (may be NULL): far-field records for the FP32 pair kernel, pair-interleaved (n_pad even)
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
-                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, Far32 *far, DevStatus *st,
+                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, Far2 *far, DevStatus *st,
                  cudaStream_t s);
 void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
                      SegCap *caps, cudaStream_t s);
@@ -47,7 +47,7 @@ struct MapArgs {
     int64_t ntiles;          // pixel tiles
     const Seg32 *s32;
     const Seg64 *s64;
-    const Far32 *far;        // far-field records (FP32 kernel)
+    const Far2 *far;         // far-field records of sample pairs (FP32 kernels)
     const SegCap *scaps;
     int64_t nst;             // segment tiles
     int split;               // segment chunks
@@ -58,6 +58,7 @@ struct MapArgs {
     int accumulate;
     DevStatus *st;
     int64_t tile_stride;     // 1; > 1 only when timing variants: every tile_stride-th pixel tile
+    unsigned long long *queue;   // FP32 passes: work counters (far pass, near pass), zero at launch
 };
 struct Variant {
     int threads, ppt, seg_tile, tx, ty;

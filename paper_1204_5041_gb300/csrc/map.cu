@@ -33,19 +33,37 @@ __device__ __forceinline__ int classify(const float4 &pc, const SegCap &sc, floa
     return gap >= d_far ? kFar : kMid;
 }
 
-// Far-field pass: every segment tile whose class is kFar, in the completed-square form
-// (Far32 records, 14 FP32 ops + 1 rcp per pair); other tiles are skipped here and summed by
-// the near-field pass.  A skipped stage still completes its mbarrier phase (zero-byte arrive).
+// Dynamic work distribution: block-wide fetch of the next (pixel tile, segment chunk) item from
+// a global counter.  Each item's arithmetic and output slots do not depend on which block takes
+// it, so the result is the same as with a static assignment; only the load balance changes
+// (near-field work is concentrated on the pixel tiles close to strings).
+__device__ __forceinline__ int64_t next_item(unsigned long long *counter, int64_t *slot)
+{
+    if (threadIdx.x == 0) *slot = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t item = *slot;
+    __syncthreads();
+    return item;
+}
+
+// Far-field pass: every segment tile whose class is kFar, in the completed-square form with
+// the numerator factored, t = [(B2 - A2)(B2 + A2) + K] / (B hs), two samples at a time in packed
+// f32x2 arithmetic (Far2 records: 7 f32x2 instructions + 1 rcp per pair); other tiles are
+// skipped here and summed by the near-field pass.  A skipped stage still completes its
+// mbarrier phase (zero-byte arrive).
 template <int NT, int P, int S, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
 {
     constexpr int TILE = NT * P;
     extern __shared__ __align__(128) unsigned char smem[];
-    Far32 *sbuf = reinterpret_cast<Far32 *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * S * sizeof(Far32));
+    static_assert(S % 2 == 0, "segment tiles hold whole sample pairs");
+    constexpr int S2 = S / 2;
+    Far2 *sbuf = reinterpret_cast<Far2 *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * S2 * sizeof(Far2));
     __shared__ int s_abort;
     __shared__ int s_cls[kStages];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t one2 = f2_pack(1.f, 1.f);
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
@@ -54,21 +72,25 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
     __syncthreads();
 
     uint32_t g = 0;
+    __shared__ int64_t s_item;
     const int64_t n_items = (a.ntiles + a.tile_stride - 1) / a.tile_stride * a.split;
     const int64_t tot = a.ntiles * TILE;
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    for (int64_t item = next_item(&a.queue[0], &s_item); item < n_items; item = next_item(&a.queue[0], &s_item)) {
         const int64_t tile = item / a.split * a.tile_stride;
         const int kc = (int)(item % a.split);
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
         const int nt = (int)(j1 - j0);
 
-        float nh[P][3], ahi[P], alo[P];
+        uint64_t n2[P][3];   // pixel direction, each component duplicated into both halves
+        float ahi[P], alo[P];
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
-            nh[q][0] = __double2float_rn(a.nv[k]);
-            nh[q][1] = __double2float_rn(a.nv[a.ldn + k]);
-            nh[q][2] = __double2float_rn(a.nv[2 * a.ldn + k]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float v = __double2float_rn(a.nv[c * a.ldn + k]);
+                n2[q][c] = f2_pack(v, v);
+            }
             ahi[q] = 0.f;
             alo[q] = 0.f;
         }
@@ -78,8 +100,8 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
             const int cls = classify(pc, a.scaps[j], a.d_far);
             s_cls[b] = cls;
             if (cls == kFar) {
-                mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Far32)));
-                bulk_g2s(sbuf + (size_t)b * S, a.far + j * S, (uint32_t)(S * sizeof(Far32)), &bars[b]);
+                mbar_arrive_expect_tx(&bars[b], (uint32_t)(S2 * sizeof(Far2)));
+                bulk_g2s(sbuf + (size_t)b * S2, a.far + j * S2, (uint32_t)(S2 * sizeof(Far2)), &bars[b]);
             } else {
                 mbar_arrive_expect_tx(&bars[b], 0u);
             }
@@ -95,25 +117,34 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
                 s_abort = 1;
             } else if (s_cls[buf] == kFar) {
-                const Far32 *fr = sbuf + (size_t)buf * S;
-                float part[P];
+                const ulonglong2 *fr = reinterpret_cast<const ulonglong2 *>(sbuf + (size_t)buf * S2);
+                uint64_t part[P];
 #pragma unroll
-                for (int q = 0; q < P; ++q) part[q] = 0.f;
+                for (int q = 0; q < P; ++q) part[q] = 0ull;   // (+0, +0)
 #pragma unroll 2
-                for (int s = 0; s < S; ++s) {
-                    const float4 ra = fr[s].a, rb = fr[s].b, rc = fr[s].c, rd = fr[s].d;
+                for (int s = 0; s < S2; ++s) {
+                    // (a.x, a.y) (a.z, a.w) (b.x, b.y) (b.z, b.w) (c.x, c.y) (c.z, c.w) (d.x, d.y),
+                    // every entry a pair over the two samples
+                    const ulonglong2 r0 = fr[7 * s], r1 = fr[7 * s + 1], r2 = fr[7 * s + 2], r3 = fr[7 * s + 3];
+                    const ulonglong2 r4 = fr[7 * s + 4], r5 = fr[7 * s + 5], r6 = fr[7 * s + 6];
 #pragma unroll
                     for (int q = 0; q < P; ++q) {
-                        const float hs = fmaf(nh[q][2], ra.z, fmaf(nh[q][1], ra.y, fmaf(nh[q][0], ra.x, ra.w)));
-                        const float B = fmaf(nh[q][2], rb.z, fmaf(nh[q][1], rb.y, fmaf(nh[q][0], rb.x, 1.f)));
-                        const float A2 = fmaf(nh[q][2], rc.z, fmaf(nh[q][1], rc.y, fmaf(nh[q][0], rc.x, rc.w)));
-                        const float B2 = fmaf(rd.x, B, rb.w);
-                        const float num = fmaf(B2, B2, fmaf(-A2, A2, rd.y));
-                        part[q] = fmaf(num, rcp_approx(B * hs), part[q]);
+                        const uint64_t hs = f2_fma(n2[q][2], r1.x, f2_fma(n2[q][1], r0.y, f2_fma(n2[q][0], r0.x, r1.y)));
+                        const uint64_t B = f2_fma(n2[q][2], r3.x, f2_fma(n2[q][1], r2.y, f2_fma(n2[q][0], r2.x, one2)));
+                        const uint64_t A2 = f2_fma(n2[q][2], r5.x, f2_fma(n2[q][1], r4.y, f2_fma(n2[q][0], r4.x, r5.y)));
+                        const uint64_t B2 = f2_fma(r6.x, B, r3.y);
+                        const uint64_t num = f2_fma(f2_sub(B2, A2), f2_add(B2, A2), r6.y);
+                        float d0, d1;
+                        f2_unpack(f2_mul(B, hs), d0, d1);
+                        part[q] = f2_fma(num, f2_pack(rcp_approx(d0), rcp_approx(d1)), part[q]);
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < P; ++q) fold(ahi[q], alo[q], part[q]);
+                for (int q = 0; q < P; ++q) {
+                    float lo, hi;
+                    f2_unpack(part[q], lo, hi);
+                    fold(ahi[q], alo[q], lo + hi);
+                }
             }
             __syncthreads();
             if (s_abort) break;
@@ -151,7 +182,7 @@ template <int NT, int P, int S>
 __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
 {
     constexpr int TILE = NT * P;
-    constexpr size_t kStageBytes = S * (sizeof(Seg32) + sizeof(Far32));   // both record types
+    constexpr size_t kStageBytes = S * sizeof(Seg32);
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sbuf = smem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
@@ -167,9 +198,10 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
     __syncthreads();
     unsigned nearcnt = 0, zerocnt = 0;
     uint32_t g = 0;
+    __shared__ int64_t s_item;
     const int64_t n_items = (a.ntiles + a.tile_stride - 1) / a.tile_stride * a.split;
     const int64_t tot = a.ntiles * TILE;
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    for (int64_t item = next_item(&a.queue[1], &s_item); item < n_items; item = next_item(&a.queue[1], &s_item)) {
         const int64_t tile = item / a.split * a.tile_stride;
         const int kc = (int)(item % a.split);
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
@@ -218,7 +250,6 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
                     unsigned char *dst = sbuf + (size_t)b * kStageBytes;
                     mbar_arrive_expect_tx(&bars[b], (uint32_t)kStageBytes);
                     bulk_g2s(dst, a.s32 + found * S, (uint32_t)(S * sizeof(Seg32)), &bars[b]);
-                    bulk_g2s(dst + S * sizeof(Seg32), a.far + found * S, (uint32_t)(S * sizeof(Far32)), &bars[b]);
                 } else {
                     mbar_arrive_expect_tx(&bars[b], 0u);
                 }
@@ -239,14 +270,14 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
                 if (j >= 0) {
                     const int cls = s_cls[buf];
                     const Seg32 *sb = reinterpret_cast<const Seg32 *>(sbuf + (size_t)buf * kStageBytes);
-                    const Far32 *fr = reinterpret_cast<const Far32 *>(sbuf + (size_t)buf * kStageBytes +
-                                                                      S * sizeof(Seg32));
                     float part[P];
 #pragma unroll
                     for (int q = 0; q < P; ++q) part[q] = 0.f;
                     if (cls == kMid) {
-                        // per warp and sample: the far-field form when every pair of the warp has
-                        // 1 - n.Xhat >= d_far^2/2 (with a margin for its FP32 rounding)
+                        // per warp and sample: when every pair of the warp has 1 - n.Xhat >= d_far^2/2
+                        // (with a margin for its FP32 rounding), the direct far-field form
+                        // t = (c/2) [B (Xdot.d) - A (X'.d)] / [B (1 - n.Xhat)] with Xdot.d = B - e and
+                        // X'.d = A - f from the sample record; else the float-pair form in d
                         const float hmin = 0.5f * a.d_far * a.d_far * 1.001f + 1e-6f;
                         for (int s = 0; s < S; ++s) {
                             const float4 ra = sb[s].a;
@@ -257,21 +288,19 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
                                 h[q] = fmaf(-nh[q][2], ra.z, fmaf(-nh[q][1], ra.y, fmaf(-nh[q][0], ra.x, 1.f)));
                                 ok = ok && (h[q] >= hmin);
                             }
+                            const float4 rd = sb[s].d, re = sb[s].e;
                             if (__all_sync(0xffffffffu, ok)) {
-                                const float4 fa = fr[s].a, fb = fr[s].b, fc = fr[s].c, fd = fr[s].d;
+                                const float ch = 0.5f * ra.w;
 #pragma unroll
                                 for (int q = 0; q < P; ++q) {
-                                    const float hs = fmaf(nh[q][2], fa.z, fmaf(nh[q][1], fa.y, fmaf(nh[q][0], fa.x, fa.w)));
-                                    const float B = fmaf(nh[q][2], fb.z, fmaf(nh[q][1], fb.y, fmaf(nh[q][0], fb.x, 1.f)));
-                                    const float A2 =
-                                        fmaf(nh[q][2], fc.z, fmaf(nh[q][1], fc.y, fmaf(nh[q][0], fc.x, fc.w)));
-                                    const float B2 = fmaf(fd.x, B, fb.w);
-                                    const float num = fmaf(B2, B2, fmaf(-A2, A2, fd.y));
-                                    part[q] = fmaf(num, rcp_approx(B * hs), part[q]);
+                                    const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
+                                    const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
+                                    const float num = fmaf(B, B - rd.w, -A * (A - re.w));
+                                    part[q] = fmaf(ch * num, rcp_approx(B * h[q]), part[q]);
                                 }
                                 continue;
                             }
-                            const float4 rb = sb[s].b, rd = sb[s].d, re = sb[s].e;
+                            const float4 rb = sb[s].b;
 #pragma unroll
                             for (int q = 0; q < P; ++q) {
                                 const float dx = (nh[q][0] - ra.x) + (nl[q][0] - rb.x);
@@ -513,13 +542,13 @@ const VEntry kF32[] = {ISW_F32_VARIANTS(ISW_ENTRY)};
 #undef ISW_ENTRY
 constexpr int kF64NT = 128, kF64P = 2, kF64S = 32;
 
-size_t smem_f32(int S) { return kStages * S * sizeof(Far32) + kStages * sizeof(uint64_t); }
+size_t smem_f32(int S) { return kStages * (S / 2) * sizeof(Far2) + kStages * sizeof(uint64_t); }
 // Stages above the default 48 KB of dynamic shared memory need the opt-in attribute.
 void allow_smem(const void *fn, size_t bytes)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
-size_t smem_near(int S) { return kStages * S * (sizeof(Seg32) + sizeof(Far32)) + kStages * sizeof(uint64_t); }
+size_t smem_near(int S) { return kStages * S * sizeof(Seg32) + kStages * sizeof(uint64_t); }
 size_t smem_f64(int S) { return kStages * S * sizeof(Seg64) + kStages * sizeof(uint64_t); }
 }  // namespace
 

@@ -92,13 +92,14 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     size_t off[8];
     size_t at = 0;
     off[0] = at; at += up256(sizeof(DevStatus));
+    const size_t off_queue = at; at += up256(2 * sizeof(unsigned long long));
     off[1] = at; at += up256((size_t)tot * 3 * sizeof(double));
     off[2] = at; at += up256((size_t)tot * sizeof(int64_t));
     off[3] = at; at += up256((size_t)ntiles * sizeof(float4));
     off[4] = at; at += up256((size_t)n_pad * sizeof(Seg32));
     off[5] = at; at += up256((size_t)n_pad * sizeof(Seg64));
     off[6] = at; at += up256((size_t)nst * sizeof(SegCap));
-    const size_t off_far = at; at += up256((size_t)n_pad * sizeof(Far32));
+    const size_t off_far = at; at += up256((size_t)(n_pad / 2) * sizeof(Far2));
     off[7] = at;
     if (at > kStaticScratchBytes) return ISW_EINVAL;  // problem too large for the static scratch
     const int64_t room = (int64_t)((kStaticScratchBytes - at) / ((size_t)tot * sizeof(double)));
@@ -133,12 +134,15 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     SegCap *scaps = (SegCap *)(b + off[6]);
     double *partial = (double *)(b + off[7]);
 
-    // the status word is the only scratch read before it is written in this call
+    // the status word and the two work counters are the only scratch read before it is written
+    // in this call
+    unsigned long long *queue = (unsigned long long *)(b + off_queue);
     if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return ISW_ECUDA;
+    if (cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return ISW_ECUDA;
     const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     launch_pixel_table(nside, full ? 0 : 1, pix0, npix, nullptr, v.tx, v.ty, ntiles, nv, tot, outidx, pcaps, st, s);
-    Far32 *far = (Far32 *)(b + off_far);
+    Far2 *far = (Far2 *)(b + off_far);
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, s32, s64, far, st, s);
     launch_seg_caps(s32, s64, n, n_pad, S, 0.01f, scaps, s);
     MapArgs a;
@@ -160,6 +164,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.accumulate = 0;
     a.st = st;
     a.tile_stride = 1;
+    a.queue = queue;
     const int64_t items = ntiles * split;
     launch_map_f32c(0, a, (int)(items < slots ? items : slots), s);
     launch_map_f32c_near(0, a, sms, s);

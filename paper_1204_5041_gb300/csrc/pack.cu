@@ -57,7 +57,7 @@ __device__ __forceinline__ void unit_dd(const double r[3], double hi[3], double 
 
 __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, double xo0, double xo1, double xo2,
                        double GU, double theta_pix, double near_k, int64_t n_pad, Seg32 *__restrict__ s32,
-                       Seg64 *__restrict__ s64, Far32 *__restrict__ far, DevStatus *ds)
+                       Seg64 *__restrict__ s64, Far2 *__restrict__ far, DevStatus *ds)
 {
     unsigned long long bad = 0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
@@ -148,12 +148,14 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
             const double xh[3] = {g.xh[0] + g.xl[0], g.xh[1] + g.xl[1], g.xh[2] + g.xl[2]};
             const double e1 = 1.0 + (g.xd[0] * xh[0] + g.xd[1] * xh[1] + g.xd[2] * xh[2]);
             const double f1 = g.xp[0] * xh[0] + g.xp[1] * xh[1] + g.xp[2] * xh[2];
-            Far32 r;
-            r.a = make_float4((float)(-sg * xh[0]), (float)(-sg * xh[1]), (float)(-sg * xh[2]), (float)sg);
-            r.b = make_float4((float)g.xd[0], (float)g.xd[1], (float)g.xd[2], (float)(-0.5 * sq * e1));
-            r.c = make_float4((float)(sq * g.xp[0]), (float)(sq * g.xp[1]), (float)(sq * g.xp[2]), (float)(-0.5 * sq * f1));
-            r.d = make_float4((float)sq, (float)(fabs(ch) * 0.25 * (f1 * f1 - e1 * e1)), 0.f, 0.f);
-            far[s] = r;
+            const float v[kFarConsts] = {(float)(-sg * xh[0]), (float)(-sg * xh[1]), (float)(-sg * xh[2]), (float)sg,
+                                         (float)g.xd[0], (float)g.xd[1], (float)g.xd[2], (float)(-0.5 * sq * e1),
+                                         (float)(sq * g.xp[0]), (float)(sq * g.xp[1]), (float)(sq * g.xp[2]),
+                                         (float)(-0.5 * sq * f1), (float)sq,
+                                         (float)(fabs(ch) * 0.25 * (f1 * f1 - e1 * e1))};
+            float *dst = reinterpret_cast<float *>(far + (s >> 1)) + (s & 1);
+#pragma unroll
+            for (int k = 0; k < kFarConsts; ++k) dst[2 * k] = v[k];
         }
     }
     if (bad) {
@@ -265,7 +267,7 @@ __global__ void k_seg_caps(const Seg32 *__restrict__ s32, const Seg64 *__restric
 }
 
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
-                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, Far32 *far, DevStatus *st,
+                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, Far2 *far, DevStatus *st,
                  cudaStream_t s)
 {
     if (n_pad <= 0) return;
