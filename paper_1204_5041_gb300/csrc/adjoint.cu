@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
     const int NG = a.ngrad;   // 6, or 9 / 10 with NG9
     unsigned nearcnt = 0, zerocnt = 0;
     uint32_t gl = 0;
+    __shared__ int64_t s_item;
     const int64_t n_items = a.nseg_tiles * a.split;
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    for (int64_t item = next_item(a.queue, &s_item); item < n_items; item = next_item(a.queue, &s_item)) {
         const int64_t st = item / a.split;
         const int kc = (int)(item - st * a.split);
         const int64_t p0 = a.npix_tiles * kc / a.split, p1 = a.npix_tiles * (kc + 1) / a.split;
@@ -319,8 +320,9 @@ __global__ void __launch_bounds__(NT) k_adj_f64(AdjArgs a)
     const int NG = a.ngrad;
     unsigned zerocnt = 0;
     uint32_t gl = 0;
+    __shared__ int64_t s_item;
     const int64_t n_items = a.nseg_tiles * a.split;
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    for (int64_t item = next_item(a.queue, &s_item); item < n_items; item = next_item(a.queue, &s_item)) {
         const int64_t st = item / a.split;
         const int kc = (int)(item - st * a.split);
         const int64_t p0 = a.npix_tiles * kc / a.split, p1 = a.npix_tiles * (kc + 1) / a.split;

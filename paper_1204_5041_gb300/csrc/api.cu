@@ -214,7 +214,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     if ((r = ensure_ws(c, kWsScap, (size_t)nst * sizeof(SegCap)))) return r;
     if (prec == ISW_F32C && (r = ensure_ws(c, kWsFar, (size_t)(n_pad / 2) * sizeof(Far2)))) return r;
     if (split > 1 && (r = ensure_ws(c, kWsPartial, (size_t)split * pp.tot * sizeof(double)))) return r;
-    if (prec == ISW_F32C && (r = ensure_ws(c, kWsQueue, 2 * sizeof(unsigned long long)))) return r;
+    if ((r = ensure_ws(c, kWsQueue, 2 * sizeof(unsigned long long)))) return r;
 
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     double *nv = (double *)c->ws[kWsNv];
@@ -252,7 +252,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.partial = split > 1 ? (double *)c->ws[kWsPartial] : nullptr;
     a.accumulate = accumulate;
     a.st = c->d_status;
-    a.queue = prec == ISW_F32C ? (unsigned long long *)c->ws[kWsQueue] : nullptr;
+    a.queue = (unsigned long long *)c->ws[kWsQueue];
     // timing a variant: every k-th pixel tile (all its segment chunks), about tune_waves waves
     a.tile_stride = 1;
     if (tune_waves > 0) {
@@ -264,9 +264,9 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     if (tuned_pixels) *tuned_pixels = (pp.ntiles + a.tile_stride - 1) / a.tile_stride * (v.tx * v.ty);
     // the timed pair work: far pass (or the FP64 kernel), chunk reduce, near-field pass
     const int ti = timing_begin(c, s);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync(work counters)");
     if (prec == ISW_F32C) {
-        cudaError_t e = cudaMemsetAsync(a.queue, 0, 2 * sizeof(unsigned long long), s);
-        if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync(work counters)");
         launch_map_f32c(vidx, a, grid, s);
         // near-field pass: adds the segment tiles the far pass skipped, chunk by chunk
         launch_map_f32c_near(vidx, a, c->num_sms, s);
@@ -581,6 +581,7 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     if ((r = ensure_ws(c, kWsS64, (size_t)n_pad * sizeof(Seg64)))) return r;
     if ((r = ensure_ws(c, kWsScap, (size_t)nseg_tiles * sizeof(SegCap)))) return r;
     if (split > 1 && (r = ensure_ws(c, kWsAdjPartial, (size_t)split * ngrad * n_pad * sizeof(double)))) return r;
+    if ((r = ensure_ws(c, kWsQueue, 2 * sizeof(unsigned long long)))) return r;
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     double *nv = (double *)c->ws[kWsNv];
     int64_t *outidx = (int64_t *)c->ws[kWsOut];
@@ -619,9 +620,12 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     a.ld_g = ld_g;
     a.partial = split > 1 ? (double *)c->ws[kWsAdjPartial] : nullptr;
     a.st = c->d_status;
+    a.queue = (unsigned long long *)c->ws[kWsQueue];
     const int64_t items = nseg_tiles * split;
     const int grid = (int)(items < slots ? items : slots);
     const int ti = timing_begin(c, s);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync(work counter)");
     launch_adjoint(prec, a, grid, s);
     timing_end(c, ti, s);
     c->n_pair += 1;

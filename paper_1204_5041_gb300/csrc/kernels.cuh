@@ -58,7 +58,7 @@ struct MapArgs {
     int accumulate;
     DevStatus *st;
     int64_t tile_stride;     // 1; > 1 only when timing variants: every tile_stride-th pixel tile
-    unsigned long long *queue;   // FP32 passes: work counters (far pass, near pass), zero at launch
+    unsigned long long *queue;   // work counters (far pass or FP64 kernel, near pass), zero at launch
 };
 struct Variant {
     int threads, ppt, seg_tile, tx, ty;
@@ -93,6 +93,7 @@ struct AdjArgs {
     int64_t ld_g;
     double *partial;         // [split][ngrad][n_pad] when split > 1
     DevStatus *st;
+    unsigned long long *queue;   // work counter, zero at launch
 };
 int adj_seg_tile(int prec);
 int adj_pix_tile(int prec);

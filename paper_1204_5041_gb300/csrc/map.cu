@@ -33,19 +33,6 @@ __device__ __forceinline__ int classify(const float4 &pc, const SegCap &sc, floa
     return gap >= d_far ? kFar : kMid;
 }
 
-// Dynamic work distribution: block-wide fetch of the next (pixel tile, segment chunk) item from
-// a global counter.  Each item's arithmetic and output slots do not depend on which block takes
-// it, so the result is the same as with a static assignment; only the load balance changes
-// (near-field work is concentrated on the pixel tiles close to strings).
-__device__ __forceinline__ int64_t next_item(unsigned long long *counter, int64_t *slot)
-{
-    if (threadIdx.x == 0) *slot = (int64_t)atomicAdd(counter, 1ull);
-    __syncthreads();
-    const int64_t item = *slot;
-    __syncthreads();
-    return item;
-}
-
 // Far-field pass: every segment tile whose class is kFar, in the completed-square form with
 // the numerator factored, t = [(B2 - A2)(B2 + A2) + K] / (B hs), two samples at a time in packed
 // f32x2 arithmetic (Far2 records: 7 f32x2 instructions + 1 rcp per pair); other tiles are
@@ -423,9 +410,10 @@ __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
     __syncthreads();
     unsigned zerocnt = 0;
     uint32_t g = 0;
+    __shared__ int64_t s_item;
     const int64_t n_items = a.ntiles * a.split;
     const int64_t tot = a.ntiles * TILE;
-    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    for (int64_t item = next_item(&a.queue[0], &s_item); item < n_items; item = next_item(&a.queue[0], &s_item)) {
         const int64_t tile = item / a.split;
         const int kc = (int)(item - tile * a.split);
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;

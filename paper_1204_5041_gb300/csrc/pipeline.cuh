@@ -62,4 +62,17 @@ __device__ __forceinline__ void drain(uint64_t *bars, uint32_t g, int i, int nt)
     }
 }
 
+// Dynamic work distribution: block-wide fetch of the next work item from
+// a global counter.  Each item's arithmetic and output slots do not depend on which block takes
+// it, so the result is the same as with a static assignment; only the load balance changes
+// (near-field work is concentrated where pixels and strings are close).
+__device__ __forceinline__ int64_t next_item(unsigned long long *counter, int64_t *slot)
+{
+    if (threadIdx.x == 0) *slot = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t item = *slot;
+    __syncthreads();
+    return item;
+}
+
 }  // namespace isw
