@@ -78,6 +78,16 @@ def lib():
                                                _dp, ctypes.c_int64, ctypes.c_int, _dp, ctypes.c_int64, _dp,
                                                ctypes.c_int64]
             L.or_lightcone_adjoint.restype = ctypes.c_int
+            L.or_atan2_quarter.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.or_atan2_quarter.restype = ctypes.c_double
+            L.or_vec2pix_ring.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, ctypes.c_int64, _i64p]
+            L.or_vec2pix_ring.restype = None
+            L.or_box_place.argtypes = [_dp, ctypes.c_int64, _i64p, ctypes.c_int64, ctypes.c_int64, _i64p, _dp,
+                                       _dp, ctypes.c_int64, _i64p]
+            L.or_box_place.restype = ctypes.c_int
+            L.or_cone_cut.argtypes = [_dp, ctypes.c_int64, _i64p, ctypes.c_int64, ctypes.c_int64, _i64p, _dp,
+                                      _dp, _dp, _dp, ctypes.c_int64, _i64p]
+            L.or_cone_cut.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -282,3 +292,57 @@ def lightcone_adjoint(mode: int, nodes, loop_params, tau, grad_samples, t_box: f
     if st:
         raise ValueError(f"or_lightcone_adjoint failed with status {st}")
     return gn, gP
+
+
+def atan2_quarter(y: float, x: float) -> float:
+    """atan2(y, x) in quarter turns, in [0, 4) (own series)."""
+    return lib().or_atan2_quarter(float(y), float(x))
+
+
+def vec2pix_ring(nside: int, vec):
+    """RING pixel of each direction (columns of vec [3, n], not necessarily unit)."""
+    vec = _c64(vec)
+    n = vec.shape[1]
+    pix = np.empty(n, dtype=np.int64)
+    lib().or_vec2pix_ring(int(nside), _d(vec), n, n, pix.ctypes.data_as(_i64p))
+    return pix
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def box_place(nodes_box, box_off, shell_box, place):
+    """Nodes of shell k = box shell_box[k] placed by place[k] (R row-major, T): returns
+    (nodes [10, n_out], shell_off_out)."""
+    nodes_box = _c64(nodes_box)
+    box_off, shell_box = _i64(box_off), _i64(shell_box)
+    place = _c64(place).reshape(-1, 12)
+    nshell = shell_box.size
+    n_out = int(sum(box_off[b + 1] - box_off[b] for b in shell_box))
+    out = np.zeros((10, max(n_out, 1)))
+    off = np.zeros(nshell + 1, dtype=np.int64)
+    st = lib().or_box_place(_d(nodes_box), nodes_box.shape[1], box_off.ctypes.data_as(_i64p), box_off.size - 1,
+                            nshell, shell_box.ctypes.data_as(_i64p), _d(place), _d(out), out.shape[1],
+                            off.ctypes.data_as(_i64p))
+    if st:
+        raise ValueError(f"or_box_place failed with status {st}")
+    return out[:, :n_out], off
+
+
+def cone_cut(samples, shell_off, nside_hz, cone_pix, r_lo, r_hi, x_obs=(0.0, 0.0, 0.0)):
+    """Samples of each shell inside its HEALPix cone and radius range, input order kept:
+    returns (kept [10, m], shell_off_out)."""
+    samples = _c64(samples)
+    shell_off = _i64(shell_off)
+    nshell = shell_off.size - 1
+    cone_pix = _i64(cone_pix)
+    r_lo, r_hi = _c64(r_lo), _c64(r_hi)
+    out = np.zeros((10, max(samples.shape[1], 1)))
+    off = np.zeros(nshell + 1, dtype=np.int64)
+    m = lib().or_cone_cut(_d(samples), samples.shape[1], shell_off.ctypes.data_as(_i64p), nshell, int(nside_hz),
+                          cone_pix.ctypes.data_as(_i64p), _d(r_lo), _d(r_hi), _d(_c64(x_obs)), _d(out),
+                          out.shape[1], off.ctypes.data_as(_i64p))
+    if m < 0:
+        raise ValueError("or_cone_cut failed")
+    return out[:, :m], off

@@ -20,6 +20,8 @@
  *   6. the analytic adjoint of the sum with respect to X and Xdot (optionally X', dsigma)
  *   7. the adjoint of the light-cone solve (implicit-function theorem on the crossing
  *      condition): gradients of LINEAR box-time nodes and of BURDEN loop parameters
+ *   8. stacking with HEALPix cones (Sec. III.B): own atan2, RING vec2pix, box placement,
+ *      cone cut
  *
  * Pins (tests/test_oracle_*.py) tie each part to something other than itself; see the
  * header comment of each section for what pins it.
@@ -807,4 +809,154 @@ int or_lightcone_adjoint(int mode, const double *nodes, int64_t n, int64_t ld,
         free(cmp);
     }
     return worst;
+}
+
+/* ------------------------------------------------------------------------------------
+ * 8. Stacking with HEALPix cones (Sec. III.B, Fig. 1): the comoving volume is voxelised by
+ * the cones that subtend the pixels of a coarse HEALPix grid (N_side^hz); each cone is
+ * filled from a simulation box rotated to face the observer, one box serving several cones
+ * (the paper reuses each run three times), and only the strings inside the cone between
+ * two radii are kept.
+ *
+ * (a) atan2 in quarter turns, own series: reduce to a = min/max of |x|, |y| in [0, 1];
+ *     a > tan(pi/8) goes to (a - 1)/(a + 1) with pi/4 added back; one half-angle step
+ *     atan(a) = 2 atan(a / (1 + sqrt(1 + a^2))) leaves |v| <= 0.2; atan(v) by its Taylor
+ *     series v (1 - v^2/3 + v^4/5 - ...), 13 terms summed from the smallest; the octant is
+ *     unfolded exactly.  Pinned against mpmath (<= 4 ulp).
+ * (b) RING vec2pix: the published HEALPix assignment (Gorski et al. 2005): z = cos(theta),
+ *     t = phi / (pi/2) in [0, 4); equatorial belt |z| <= 2/3: the pixel's two edge-line
+ *     indices jp = floor(N (1/2 + t - 3z/4)), jm = floor(N (1/2 + t + 3z/4)) give the ring
+ *     and the position in it; polar caps: with tp = frac(t) and h = N sqrt(3 (1 - |z|)),
+ *     jp = floor(tp h), jm = floor((1 - tp) h), ring jp + jm + 1 counted from the pole and
+ *     position floor(t * ring).  Pinned by vec2pix(pix2vec(p)) = p, by an independent numpy
+ *     statement of the same rules away from pixel edges, and by equal-area counts.
+ * (c) box placement: shell k takes the nodes of box b_k and maps X -> R X + T, Xdot -> R Xdot,
+ *     X' -> R X' (R row-major, (R x)_i = (R_i0 x_0 + R_i1 x_1) + R_i2 x_2), dsigma unchanged.
+ * (d) cone cut: a light-cone sample of shell k is kept when the direction of X - x_obs lies
+ *     in RING pixel cone_pix[k] of N_side^hz and r_lo[k] <= |X - x_obs| < r_hi[k]; kept
+ *     samples keep their input order.
+ * ---------------------------------------------------------------------------------- */
+#define ATAN_TERMS 13
+
+double or_atan2_quarter(double y, double x)
+{
+    const double tan_pi_8 = 0.41421356237309504880;  /* tan(pi/8) */
+    const double two_over_pi = 0.63661977236758134308;
+    double ax = fabs(x), ay = fabs(y);
+    if (ax == 0.0 && ay == 0.0) return 0.0;
+    int swap = ay > ax;
+    double a = swap ? ax / ay : ay / ax;
+    double base = 0.0;  /* quarter turns */
+    if (a > tan_pi_8) {
+        a = (a - 1.0) / (a + 1.0);
+        base = 0.5;
+    }
+    double v = a / (1.0 + sqrt(1.0 + a * a));
+    double w = v * v;
+    double s = 0.0;
+    for (int k = ATAN_TERMS - 1; k >= 0; --k) {
+        double ck = 1.0 / (double)(2 * k + 1);
+        s = (k & 1) ? s * w - ck : s * w + ck;
+    }
+    /* s = 1 - w/3 + w^2/5 - ... (Horner: the sign of each coefficient alternates) */
+    double q = base + (2.0 * (v * s)) * two_over_pi;
+    if (swap) q = 1.0 - q;
+    if (x < 0.0) q = 2.0 - q;
+    if (y < 0.0) q = 4.0 - q;
+    if (q >= 4.0) q = q - 4.0;
+    return q;
+}
+
+int64_t or_vec2pix_ring_one(int64_t N, const double v[3])
+{
+    double r = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    double z = v[2] / r;
+    double za = fabs(z);
+    double t = or_atan2_quarter(v[1], v[0]);
+    double Nd = (double)N;
+    int64_t npix = 12 * N * N, ncap = 2 * N * (N - 1);
+    if (za <= 2.0 / 3.0) {
+        double t1 = Nd * (0.5 + t);
+        double t2 = Nd * (z * 0.75);
+        int64_t jp = (int64_t)floor(t1 - t2);
+        int64_t jm = (int64_t)floor(t1 + t2);
+        int64_t ir = N + 1 + jp - jm;              /* 1 .. 2N+1, from z = 2/3 down */
+        int64_t kshift = 1 - (ir & 1);
+        int64_t ip = (jp + jm - N + kshift + 1) / 2;
+        ip = ((ip % (4 * N)) + 4 * N) % (4 * N);
+        return ncap + (ir - 1) * 4 * N + ip;
+    }
+    double tp = t - floor(t);
+    double h = Nd * sqrt(3.0 * (1.0 - za));
+    int64_t jp = (int64_t)floor(tp * h);
+    int64_t jm = (int64_t)floor((1.0 - tp) * h);
+    int64_t ir = jp + jm + 1;                      /* ring from the nearer pole */
+    int64_t ip = (int64_t)floor(t * (double)ir);
+    ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+    if (z > 0.0) return 2 * ir * (ir - 1) + ip;
+    return npix - 2 * ir * (ir + 1) + ip;
+}
+
+/* vec: double[3][ld] (need not be normalised, not zero); pix: int64[n] */
+void or_vec2pix_ring(int64_t N, const double *vec, int64_t n, int64_t ld, int64_t *pix)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        double v[3] = {vec[k], vec[ld + k], vec[2 * ld + k]};
+        pix[k] = or_vec2pix_ring_one(N, v);
+    }
+}
+
+/* nodes_box: double[10][ldb]; box_off[nbox+1]; shell_box[nshell]; place: double[nshell][12]
+ * (R row-major, then T); out: double[10][ldo]; shell_off_out[nshell+1] (host) */
+int or_box_place(const double *nodes_box, int64_t ldb, const int64_t *box_off, int64_t nbox,
+                 int64_t nshell, const int64_t *shell_box, const double *place, double *out,
+                 int64_t ldo, int64_t *shell_off_out)
+{
+    int64_t o = 0;
+    shell_off_out[0] = 0;
+    for (int64_t k = 0; k < nshell; ++k) {
+        int64_t b = shell_box[k];
+        if (b < 0 || b >= nbox) return OR_EINVAL;
+        const double *R = place + 12 * k, *T = place + 12 * k + 9;
+        for (int64_t s = box_off[b]; s < box_off[b + 1]; ++s, ++o) {
+            if (o >= ldo) return OR_EINVAL;
+            for (int blk = 0; blk < 3; ++blk) {
+                double x[3];
+                for (int c = 0; c < 3; ++c) x[c] = nodes_box[(3 * blk + c) * ldb + s];
+                for (int i = 0; i < 3; ++i) {
+                    double y = (R[3 * i] * x[0] + R[3 * i + 1] * x[1]) + R[3 * i + 2] * x[2];
+                    out[(3 * blk + i) * ldo + o] = blk == 0 ? y + T[i] : y;
+                }
+            }
+            out[9 * ldo + o] = nodes_box[9 * ldb + s];
+        }
+        shell_off_out[k + 1] = o;
+    }
+    return OR_OK;
+}
+
+/* samples: double[10][ld], shell_off[nshell+1]; cone_pix, r_lo, r_hi per shell; out:
+ * double[10][ldo] kept samples in input order; shell_off_out[nshell+1]; returns the count
+ * (or -1 on a bad argument). */
+int64_t or_cone_cut(const double *samples, int64_t ld, const int64_t *shell_off, int64_t nshell,
+                    int64_t nside_hz, const int64_t *cone_pix, const double *r_lo,
+                    const double *r_hi, const double x_obs[3], double *out, int64_t ldo,
+                    int64_t *shell_off_out)
+{
+    int64_t o = 0;
+    shell_off_out[0] = 0;
+    for (int64_t k = 0; k < nshell; ++k) {
+        for (int64_t s = shell_off[k]; s < shell_off[k + 1]; ++s) {
+            double d[3] = {samples[s] - x_obs[0], samples[ld + s] - x_obs[1],
+                           samples[2 * ld + s] - x_obs[2]};
+            double r = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+            if (!(r >= r_lo[k] && r < r_hi[k]) || !(r > 0.0)) continue;
+            if (or_vec2pix_ring_one(nside_hz, d) != cone_pix[k]) continue;
+            if (o >= ldo) return -1;
+            for (int q = 0; q < 10; ++q) out[q * ldo + o] = samples[q * ld + s];
+            ++o;
+        }
+        shell_off_out[k + 1] = o;
+    }
+    return o;
 }
