@@ -215,13 +215,11 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
 #pragma unroll
                     for (int k = 0; k < kAcc; ++k) part[k] = 0.f;
                     if (far) {
-                        // derivatives scale as 1/Q^2: d is formed as a float pair even far away
+                        // |d| >= d_far here: d from the leading floats is accurate to ~1e-7
 #pragma unroll 2
                         for (int q = w0; q < w0 + 32; ++q) {
-                            const float4 pa = sp[q].a, pb = sp[q].b;
-                            const float dx = (pa.x - r.a.x) + (pb.x - r.b.x);
-                            const float dy = (pa.y - r.a.y) + (pb.y - r.b.y);
-                            const float dz = (pa.z - r.a.z) + (pb.z - r.b.z);
+                            const float4 pa = sp[q].a;
+                            const float dx = pa.x - r.a.x, dy = pa.y - r.a.y, dz = pa.z - r.a.z;
                             const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                             const float Pd = fmaf(r.d.z, dz, fmaf(r.d.y, dy, r.d.x * dx));
                             const float Qd = fmaf(r.e.z, dz, fmaf(r.e.y, dy, r.e.x * dx));
