@@ -147,6 +147,72 @@ __device__ __forceinline__ void pix2vec_ring(int64_t N, int64_t p, double &x, do
     y = dmul(st, sp);
 }
 
+// atan2(y, x) in quarter turns, in [0, 4): a = min/max of |x|, |y|; a > tan(pi/8) is moved to
+// (a - 1)/(a + 1) with pi/4 added back; one half-angle step atan(a) = 2 atan(a/(1 + sqrt(1 + a^2)))
+// leaves |v| <= 0.2 for the Taylor series v (1 - v^2/3 + v^4/5 - ...), 13 terms summed from the
+// smallest; the octant is unfolded exactly.  IEEE operations in a fixed order, so the result
+// (and every HEALPix pixel decided from it) is reproducible operation by operation.
+__device__ __forceinline__ double atan2_quarter(double y, double x)
+{
+    const double tan_pi_8 = 0.41421356237309504880;
+    const double two_over_pi = 0.63661977236758134308;
+    const double ax = fabs(x), ay = fabs(y);
+    if (ax == 0.0 && ay == 0.0) return 0.0;
+    const bool swap = ay > ax;
+    double a = swap ? ddiv(ax, ay) : ddiv(ay, ax);
+    double base = 0.0;
+    if (a > tan_pi_8) {
+        a = ddiv(dsub(a, 1.0), dadd(a, 1.0));
+        base = 0.5;
+    }
+    const double v = ddiv(a, dadd(1.0, dsqrt(dadd(1.0, dmul(a, a)))));
+    const double w = dmul(v, v);
+    double s = 0.0;
+    for (int k = 12; k >= 0; --k) {
+        const double ck = ddiv(1.0, (double)(2 * k + 1));
+        s = (k & 1) ? dsub(dmul(s, w), ck) : dadd(dmul(s, w), ck);
+    }
+    double q = dadd(base, dmul(dmul(2.0, dmul(v, s)), two_over_pi));
+    if (swap) q = dsub(1.0, q);
+    if (x < 0.0) q = dsub(2.0, q);
+    if (y < 0.0) q = dsub(4.0, q);
+    if (q >= 4.0) q = dsub(q, 4.0);
+    return q;
+}
+
+// RING pixel of direction v (not necessarily unit, not zero): the published HEALPix rules with
+// z = cos(theta) and t = phi/(pi/2): equatorial belt |z| <= 2/3 from the two edge-line indices
+// floor(N (1/2 + t -+ 3z/4)), polar caps from floor(frac(t) h), floor((1 - frac(t)) h) with
+// h = N sqrt(3 (1 - |z|)) and the position floor(t * ring).
+__device__ __forceinline__ int64_t vec2pix_ring(int64_t N, double vx, double vy, double vz)
+{
+    const double r = dsqrt(dadd(dadd(dmul(vx, vx), dmul(vy, vy)), dmul(vz, vz)));
+    const double z = ddiv(vz, r);
+    const double za = fabs(z);
+    const double t = atan2_quarter(vy, vx);
+    const double Nd = (double)N;
+    if (za <= 2.0 / 3.0) {
+        const double t1 = dmul(Nd, dadd(0.5, t));
+        const double t2 = dmul(Nd, dmul(z, 0.75));
+        const int64_t jp = (int64_t)floor(dsub(t1, t2));
+        const int64_t jm = (int64_t)floor(dadd(t1, t2));
+        const int64_t ir = N + 1 + jp - jm;
+        const int64_t kshift = 1 - (ir & 1);
+        int64_t ip = (jp + jm - N + kshift + 1) / 2;
+        ip = ((ip % (4 * N)) + 4 * N) % (4 * N);
+        return 2 * N * (N - 1) + (ir - 1) * 4 * N + ip;
+    }
+    const double tp = dsub(t, floor(t));
+    const double h = dmul(Nd, dsqrt(dmul(3.0, dsub(1.0, za))));
+    const int64_t jp = (int64_t)floor(dmul(tp, h));
+    const int64_t jm = (int64_t)floor(dmul(dsub(1.0, tp), h));
+    const int64_t ir = jp + jm + 1;
+    int64_t ip = (int64_t)floor(dmul(t, (double)ir));
+    ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+    if (z > 0.0) return 2 * ir * (ir - 1) + ip;
+    return 12 * N * N - 2 * ir * (ir + 1) + ip;
+}
+
 // RING index of the pixel at (ix, iy) of base face f (0..11): the twelve base pixels are
 // rhombi; face f spans rings around jr(f)*N, with jr = 2 (north faces 0-3), 3 (equatorial
 // faces 4-7), 4 (south faces 8-11), and its corner sits at longitude jp(f) * pi/4.
@@ -358,14 +424,17 @@ struct Tunables {
 // ------------------------------------------------------------------------------------
 // Host-side context
 // ------------------------------------------------------------------------------------
+// workspace slots of a context (device buffers grown on demand)
+constexpr int kMaxWorkspaces = 32;
+
 struct isw_ctx {
     int device;
     int num_sms;
     char last_error[512];
     isw::DevStatus *d_status;     // device status word + counters
     // workspace buffers (grown on demand, never shrunk)
-    void *ws[16];
-    size_t ws_size[16];
+    void *ws[kMaxWorkspaces];
+    size_t ws_size[kMaxWorkspaces];
     // tunables
     double near_k;      // near-field radius in units of max(pixel size, segment angle)
     double b_min;       // 1 + n.Xdot below this goes to FP64
