@@ -124,6 +124,15 @@ int isw_get_timing(isw_ctx *ctx, double *ms, int64_t *pair_launches, int64_t *al
 int hp_pix2vec_ring(isw_ctx *ctx, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list,
                     double *vec_out, int64_t ld_out, void *stream);
 
+/* RING pixel of arbitrary directions (the inverse of hp_pix2vec_ring; Gorski et al. 2005 rules).
+ *   vec     : device double[3][ld] directions (any positive length), ld >= n
+ *   pix_out : device int64[n]
+ * phi comes from the library's own atan2 series and every step is an IEEE operation in a fixed
+ * order, so the pixel decided for a direction is reproducible.  A zero or non-finite
+ * direction writes -1 and sets ISW_EINVAL in the device status. */
+int hp_vec2pix_ring(isw_ctx *ctx, int64_t nside, const double *vec, int64_t n, int64_t ld, int64_t *pix_out,
+                    void *stream);
+
 /* Past-light-cone intersection (Eq. 1: the string points X with X cap x_gamma; Sec. II.B:
  * X' and Xdot are recorded at the crossing).
  *   mode = ISW_LINEAR: nodes_in is double[10][ld]: X(3), Xdot(3), X'(3), dsigma at box time
@@ -143,6 +152,47 @@ int lightcone_intersect(isw_ctx *ctx, int mode, const double *nodes_in, int64_t 
                         const double *loop_params, int64_t nloops, int64_t ldp, double t_box,
                         const double *x_obs, double t_obs, double *samples_out, int64_t ld_out,
                         double *tau_out, int32_t *status, void *stream);
+
+/* lightcone_intersect for many shells in one launch (the solve isw_map_batched runs):
+ *   nodes        : device double[10][ld] of all shells; shell_off host int64[nshell+1]
+ *                  (shell_off[0] = 0), t_box host double[nshell], mode host int32[nshell]
+ *   loop_params  : as in lightcone_intersect (required when a shell is ISW_BURDEN)
+ *   samples_out  : device double[10][ld_out], ld_out >= shell_off[nshell]
+ * Non-OK nodes are recorded in the context status (read with isw_check_status). */
+int lightcone_intersect_shells(isw_ctx *ctx, const double *nodes, int64_t ld, const int64_t *shell_off,
+                               int64_t nshell, const double *t_box, const int32_t *mode, const double *loop_params,
+                               int64_t nloops, int64_t ldp, const double *x_obs, double t_obs,
+                               double *samples_out, int64_t ld_out, void *stream);
+
+/* Stacking with HEALPix cones (Sec. III.B, Fig. 1: the comoving volume is voxelised by the
+ * cones of a coarse HEALPix grid, each filled from a simulation box rotated to face the
+ * observer; one box serves several cones).
+ *
+ * box_place: shell k takes the nodes of box shell_box[k] and maps X -> R_k X + T_k,
+ * Xdot -> R_k Xdot, X' -> R_k X' (dsigma unchanged).
+ *   nodes_box     : device double[10][ld_box] of all boxes, box_off host int64[nbox+1]
+ *   shell_box     : host int64[nshell], the box of each shell (a box may serve many shells)
+ *   place         : device double[nshell][12]: R_k row-major (9), then T_k (3)
+ *   nodes_out     : device double[10][ld_out], ld_out >= the total node count
+ *   shell_off_out : host int64[nshell+1], written on return (before the kernel runs)
+ * (R x)_i is evaluated as (R_i0 x_0 + R_i1 x_1) + R_i2 x_2 in IEEE double (reproducible). */
+int box_place(isw_ctx *ctx, const double *nodes_box, int64_t ld_box, const int64_t *box_off, int64_t nbox,
+              const int64_t *shell_box, int64_t nshell, const double *place, double *nodes_out, int64_t ld_out,
+              int64_t *shell_off_out, void *stream);
+
+/* cone_cut: keep a light-cone sample of shell k when the direction of X - x_obs lies in RING
+ * pixel cone_pix[k] of resolution nside_hz and r_lo[k] <= |X - x_obs| < r_hi[k]; kept samples
+ * are compacted in input order (a stable, deterministic stream compaction).
+ *   samples       : device double[10][ld]; shell_off host int64[nshell+1]
+ *   cone_pix, r_lo, r_hi : device arrays of nshell
+ *   samples_out   : device double[10][ld_out], ld_out >= shell_off[nshell]
+ *   shell_off_out : device int64[nshell+1], kept-sample offsets of the shells
+ *   count         : host int64* or NULL; when given, the call synchronises the stream and
+ *                   writes the number of kept samples (what isw_map needs as n) */
+int cone_cut(isw_ctx *ctx, const double *samples, int64_t ld, const int64_t *shell_off, int64_t nshell,
+             int64_t nside_hz, const int64_t *cone_pix, const double *r_lo, const double *r_hi,
+             const double *x_obs, double *samples_out, int64_t ld_out, int64_t *shell_off_out, int64_t *count,
+             void *stream);
 
 /* The map of Eq. (1)-(2) (Sec. III.A: every pixel sums every sample, none cut).
  *   nside, pix0, npix, pix_list : pixels as in hp_pix2vec_ring; npix = 12 N^2 with

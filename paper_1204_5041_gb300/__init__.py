@@ -78,6 +78,12 @@ def lib():
                                            _dbl, _dbl, _i32, _i32, _i32, _vp, _vp]),
                 "lightcone_adjoint": (_i32, [_vp, _i32, _vp, _i64, _i64, _vp, _i64, _i64, _dbl, _vp, _vp, _vp,
                                              _i64, _i32, _vp, _i64, _vp, _i64, _vp]),
+                "hp_vec2pix_ring": (_i32, [_vp, _i64, _vp, _i64, _i64, _vp, _vp]),
+                "lightcone_intersect_shells": (_i32, [_vp, _vp, _i64, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp,
+                                                      _dbl, _vp, _i64, _vp]),
+                "box_place": (_i32, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _vp]),
+                "cone_cut": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp,
+                                    ctypes.POINTER(_i64), _vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -414,3 +420,112 @@ class ISWLightconeMap(torch.autograd.Function):
                              prec=prec, ngrad=10)
         gn, gl = lightcone_adjoint(mode, nodes.detach(), tau, gs, loop_params=P, t_box=t_box, x_obs=x_obs)
         return gn, (gl if has_loops else None), None, None, None, None, None, None, None, None
+
+
+def hp_vec2pix_ring(nside: int, vec, out=None, ctx=None, stream=None):
+    """RING pixel of each direction (columns of a float64 CUDA tensor [3, n]): int64 tensor [n]."""
+    c = _ctx(ctx)
+    _dev_tensor(vec, torch.float64, "vec")
+    n, ld = _rows(vec, 3, "vec")
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=vec.device)
+    _dev_tensor(out, torch.int64, "out")
+    c.check(lib().hp_vec2pix_ring(c.handle, int(nside), _ptr(vec), n, ld, _ptr(out), _stream(stream)))
+    return out
+
+
+def _host_i64(a):
+    import numpy as np
+
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def lightcone_intersect_shells(nodes, shell_off, t_box, mode, loop_params=None, x_obs=None, t_obs: float = 1.0,
+                               out=None, ctx=None, stream=None):
+    """Light-cone samples of many shells in one launch: float64 CUDA tensor [10, n]."""
+    import numpy as np
+
+    c = _ctx(ctx)
+    _dev_tensor(nodes, torch.float64, "nodes")
+    n, ld = _rows(nodes, 10, "nodes")
+    off = _host_i64(shell_off)
+    tb = np.ascontiguousarray(np.asarray(t_box, dtype=np.float64))
+    md = np.ascontiguousarray(np.asarray(mode, dtype=np.int32))
+    if off.size != tb.size + 1 or md.size != tb.size or off[-1] != n:
+        raise ValueError("shell_off must have nshell + 1 entries ending at n; t_box, mode nshell entries")
+    P, nloops, ldp = None, 0, 0
+    if loop_params is not None:
+        _dev_tensor(loop_params, torch.float64, "loop_params")
+        nloops, ldp = _rows(loop_params, 17, "loop_params")
+        P = loop_params
+    if out is None:
+        out = torch.empty((10, n), dtype=torch.float64, device=nodes.device)
+    _, ld_out = _rows(out, 10, "out")
+    c.check(lib().lightcone_intersect_shells(c.handle, _ptr(nodes), ld, off.ctypes.data_as(_vp), tb.size,
+                                             tb.ctypes.data_as(_vp), md.ctypes.data_as(_vp), _ptr(P), nloops, ldp,
+                                             _xobs(x_obs), float(t_obs), _ptr(out), ld_out, _stream(stream)))
+    return out
+
+
+def box_place(nodes_box, box_off, shell_box, place, out=None, ctx=None, stream=None):
+    """Nodes of every shell placed from its box: returns (nodes [10, n_out] CUDA tensor,
+    shell_off_out host int64 array)."""
+    import numpy as np
+
+    c = _ctx(ctx)
+    _dev_tensor(nodes_box, torch.float64, "nodes_box")
+    _, ldb = _rows(nodes_box, 10, "nodes_box")
+    boff, sbox = _host_i64(box_off), _host_i64(shell_box)
+    _dev_tensor(place, torch.float64, "place")
+    if place.numel() != 12 * sbox.size or not place.is_contiguous():
+        raise ValueError("place must be a contiguous float64 CUDA tensor [nshell, 12]")
+    n_out = int(sum(boff[b + 1] - boff[b] for b in sbox))
+    if out is None:
+        out = torch.empty((10, max(n_out, 1)), dtype=torch.float64, device=nodes_box.device)
+    _, ld_out = _rows(out, 10, "out")
+    off = np.zeros(sbox.size + 1, dtype=np.int64)
+    c.check(lib().box_place(c.handle, _ptr(nodes_box), ldb, boff.ctypes.data_as(_vp), boff.size - 1,
+                            sbox.ctypes.data_as(_vp), sbox.size, _ptr(place), _ptr(out), ld_out,
+                            off.ctypes.data_as(_vp), _stream(stream)))
+    return out[:, :n_out], off
+
+
+def cone_cut(samples, shell_off, nside_hz: int, cone_pix, r_lo, r_hi, x_obs=None, out=None, ctx=None, stream=None):
+    """Samples inside each shell's HEALPix cone and radius range, compacted in input order:
+    returns (kept [10, m] CUDA tensor view, shell offsets int64 CUDA tensor [nshell + 1]).
+    Synchronises the stream to read m."""
+    c = _ctx(ctx)
+    _dev_tensor(samples, torch.float64, "samples")
+    n, ld = _rows(samples, 10, "samples")
+    off = _host_i64(shell_off)
+    nshell = off.size - 1
+    if off[-1] != n:
+        raise ValueError("shell_off must end at the sample count")
+    for t, dt, name in ((cone_pix, torch.int64, "cone_pix"), (r_lo, torch.float64, "r_lo"),
+                        (r_hi, torch.float64, "r_hi")):
+        _dev_tensor(t, dt, name)
+        if t.numel() != nshell or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of nshell entries")
+    if out is None:
+        out = torch.empty((10, max(n, 1)), dtype=torch.float64, device=samples.device)
+    _, ld_out = _rows(out, 10, "out")
+    off_out = torch.empty(nshell + 1, dtype=torch.int64, device=samples.device)
+    cnt = _i64(0)
+    c.check(lib().cone_cut(c.handle, _ptr(samples), ld, off.ctypes.data_as(_vp), nshell, int(nside_hz),
+                           _ptr(cone_pix), _ptr(r_lo), _ptr(r_hi), _xobs(x_obs), _ptr(out), ld_out, _ptr(off_out),
+                           ctypes.byref(cnt), _stream(stream)))
+    return out[:, :cnt.value], off_out
+
+
+def isw_map_stacked(nside: int, nodes_box, box_off, shell_box, place, t_box, nside_hz: int, cone_pix, r_lo, r_hi,
+                    x_obs=None, t_obs: float = 1.0, GU: float = 1.0, prec="f32c", out=None, ctx=None, stream=None):
+    """Full-sky map of boxes stacked into HEALPix cones (Sec. III.B): box_place ->
+    lightcone_intersect_shells (LINEAR) -> cone_cut -> isw_map.  Returns (theta, kept samples)."""
+    import numpy as np
+
+    placed, off = box_place(nodes_box, box_off, shell_box, place, ctx=ctx, stream=stream)
+    mode = np.zeros(len(off) - 1, dtype=np.int32)
+    samples = lightcone_intersect_shells(placed, off, t_box, mode, x_obs=x_obs, t_obs=t_obs, ctx=ctx, stream=stream)
+    kept, _ = cone_cut(samples, off, nside_hz, cone_pix, r_lo, r_hi, x_obs=x_obs, ctx=ctx, stream=stream)
+    theta = isw_map(nside, kept, x_obs=x_obs, GU=GU, prec=prec, out=out, ctx=ctx, stream=stream)
+    return theta, kept

@@ -1,5 +1,6 @@
 // C ABI of the library (include/isw.h): argument checks, workspace, launch sequences.
 #include <cmath>
+#include <vector>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -14,8 +15,9 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsCount
 };
+static_assert(kWsCount <= kMaxWorkspaces, "isw_ctx holds kMaxWorkspaces workspace slots");
 
 int set_err(isw_ctx *c, int code, const char *fmt, ...)
 {
@@ -521,6 +523,158 @@ int lightcone_adjoint(isw_ctx *c, int mode, const double *nodes_in, int64_t n, i
                              c->d_status, s);
     c->n_launch += (n > 0 ? 1 : 0) + (mode == ISW_BURDEN ? 1 : 0);
     return check_launch(c, "lightcone_adjoint launch");
+}
+
+int hp_vec2pix_ring(isw_ctx *c, int64_t nside, const double *vec, int64_t n, int64_t ld, int64_t *pix_out,
+                    void *stream)
+{
+    if (!c) return ISW_EINVAL;
+    if (nside < 1 || nside > (1 << 24)) return set_err(c, ISW_EINVAL, "nside out of range");
+    if (n < 0) return set_err(c, ISW_EINVAL, "n < 0");
+    if (n == 0) return ISW_OK;
+    if (ld < n) return set_err(c, ISW_EINVAL, "ld < n");
+    if (!is_device_ptr(vec) || !is_device_ptr(pix_out)) return set_err(c, ISW_EINVAL, "vec and pix_out must be device pointers");
+    int r;
+    if ((r = set_device(c))) return r;
+    launch_vec2pix(nside, vec, n, ld, pix_out, c->d_status, (cudaStream_t)stream);
+    c->n_launch += 1;
+    return check_launch(c, "hp_vec2pix_ring launch");
+}
+
+// Host metadata for the stacking calls: copied to the context's device workspace after the
+// stream has drained (earlier work on it may still read the previous copy).
+static int upload_meta(isw_ctx *c, cudaStream_t s, const void *const *src, const size_t *bytes, int nsrc, void **dst)
+{
+    size_t tot = 0;
+    for (int i = 0; i < nsrc; ++i) tot += (bytes[i] + 255) / 256 * 256;
+    int r;
+    if ((r = ensure_ws(c, kWsConeMeta, tot))) return r;
+    cudaError_t e = cudaStreamSynchronize(s);
+    unsigned char *p = (unsigned char *)c->ws[kWsConeMeta];
+    for (int i = 0; i < nsrc && e == cudaSuccess; ++i) {
+        dst[i] = p;
+        if (bytes[i]) e = cudaMemcpy(p, src[i], bytes[i], cudaMemcpyHostToDevice);
+        p += (bytes[i] + 255) / 256 * 256;
+    }
+    return e == cudaSuccess ? ISW_OK : cuda_err(c, e, "metadata upload");
+}
+
+int box_place(isw_ctx *c, const double *nodes_box, int64_t ld_box, const int64_t *box_off, int64_t nbox,
+              const int64_t *shell_box, int64_t nshell, const double *place, double *nodes_out, int64_t ld_out,
+              int64_t *shell_off_out, void *stream)
+{
+    if (!c) return ISW_EINVAL;
+    if (nbox < 1 || nshell < 0 || !box_off || (nshell > 0 && (!shell_box || !shell_off_out)))
+        return set_err(c, ISW_EINVAL, "box_off (host, nbox + 1), shell_box and shell_off_out (host) are required");
+    if (box_off[0] != 0) return set_err(c, ISW_EINVAL, "box_off[0] must be 0");
+    for (int64_t b = 0; b < nbox; ++b)
+        if (box_off[b + 1] < box_off[b]) return set_err(c, ISW_EINVAL, "box_off must be non-decreasing");
+    std::vector<int64_t> off(nshell + 1), start(nshell > 0 ? nshell : 1);
+    off[0] = 0;
+    for (int64_t k = 0; k < nshell; ++k) {
+        const int64_t b = shell_box[k];
+        if (b < 0 || b >= nbox) return set_err(c, ISW_EINVAL, "shell_box[%lld] out of range", (long long)k);
+        start[k] = box_off[b];
+        off[k + 1] = off[k] + (box_off[b + 1] - box_off[b]);
+    }
+    for (int64_t k = 0; k <= nshell; ++k) shell_off_out[k] = off[k];
+    const int64_t n_out = off[nshell];
+    if (n_out == 0) return ISW_OK;
+    if (ld_box < box_off[nbox] || ld_out < n_out) return set_err(c, ISW_EINVAL, "ld_box or ld_out too small");
+    if (!is_device_ptr(nodes_box) || !is_device_ptr(place) || !is_device_ptr(nodes_out))
+        return set_err(c, ISW_EINVAL, "nodes_box, place and nodes_out must be device pointers");
+    int r;
+    if ((r = set_device(c))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *src[2] = {off.data(), start.data()};
+    const size_t bytes[2] = {(size_t)(nshell + 1) * 8, (size_t)nshell * 8};
+    void *dst[2];
+    if ((r = upload_meta(c, s, src, bytes, 2, dst))) return r;
+    launch_box_place(nodes_box, ld_box, (const int64_t *)dst[0], (const int64_t *)dst[1], nshell, place, nodes_out,
+                     ld_out, n_out, s);
+    c->n_launch += 1;
+    return check_launch(c, "box_place launch");
+}
+
+int lightcone_intersect_shells(isw_ctx *c, const double *nodes, int64_t ld, const int64_t *shell_off, int64_t nshell,
+                               const double *t_box, const int32_t *mode, const double *loop_params, int64_t nloops,
+                               int64_t ldp, const double *x_obs, double t_obs, double *samples_out, int64_t ld_out,
+                               void *stream)
+{
+    if (!c) return ISW_EINVAL;
+    if (nshell < 1 || !shell_off || !t_box || !mode)
+        return set_err(c, ISW_EINVAL, "shell_off, t_box and mode (host arrays) are required");
+    if (shell_off[0] != 0) return set_err(c, ISW_EINVAL, "shell_off[0] must be 0");
+    bool burden = false;
+    for (int64_t k = 0; k < nshell; ++k) {
+        if (shell_off[k + 1] < shell_off[k]) return set_err(c, ISW_EINVAL, "shell_off must be non-decreasing");
+        if (mode[k] != ISW_LINEAR && mode[k] != ISW_BURDEN) return set_err(c, ISW_EINVAL, "unknown mode");
+        if (mode[k] == ISW_LINEAR && !(t_obs > t_box[k])) return set_err(c, ISW_EINVAL, "t_obs must exceed t_box");
+        burden = burden || mode[k] == ISW_BURDEN;
+    }
+    const int64_t n = shell_off[nshell];
+    int r;
+    if ((r = check_samples(c, nodes, n, ld))) return r;
+    if (n == 0) return ISW_OK;
+    if (ld_out < n || !is_device_ptr(samples_out)) return set_err(c, ISW_EINVAL, "samples_out: device, ld_out >= n");
+    if (burden && (nloops <= 0 || ldp < nloops || !is_device_ptr(loop_params)))
+        return set_err(c, ISW_EINVAL, "BURDEN shells need device loop_params[17][ldp], ldp >= nloops > 0");
+    if (!std::isfinite(t_obs)) return set_err(c, ISW_EINVAL, "t_obs not finite");
+    if ((r = set_device(c))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *src[3] = {shell_off, t_box, mode};
+    const size_t bytes[3] = {(size_t)(nshell + 1) * 8, (size_t)nshell * 8, (size_t)nshell * 4};
+    void *dst[3];
+    if ((r = upload_meta(c, s, src, bytes, 3, dst))) return r;
+    const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
+    const double tol = 4.0 * (std::nextafter(t_obs, INFINITY) - t_obs);
+    launch_lightcone_shells(nodes, n, ld, (const int64_t *)dst[0], nshell, (const double *)dst[1],
+                            (const int32_t *)dst[2], loop_params, nloops, ldp, xo[0], xo[1], xo[2], t_obs, tol,
+                            samples_out, ld_out, c->d_status, s);
+    c->n_launch += 1;
+    return check_launch(c, "lightcone_intersect_shells launch");
+}
+
+int cone_cut(isw_ctx *c, const double *samples, int64_t ld, const int64_t *shell_off, int64_t nshell, int64_t nside_hz,
+             const int64_t *cone_pix, const double *r_lo, const double *r_hi, const double *x_obs,
+             double *samples_out, int64_t ld_out, int64_t *shell_off_out, int64_t *count, void *stream)
+{
+    if (!c) return ISW_EINVAL;
+    if (nshell < 1 || !shell_off) return set_err(c, ISW_EINVAL, "shell_off (host, nshell + 1) is required");
+    if (nside_hz < 1 || nside_hz > (1 << 24)) return set_err(c, ISW_EINVAL, "nside_hz out of range");
+    if (shell_off[0] != 0) return set_err(c, ISW_EINVAL, "shell_off[0] must be 0");
+    for (int64_t k = 0; k < nshell; ++k)
+        if (shell_off[k + 1] < shell_off[k]) return set_err(c, ISW_EINVAL, "shell_off must be non-decreasing");
+    const int64_t n = shell_off[nshell];
+    int r;
+    if ((r = check_samples(c, samples, n, ld))) return r;
+    if (!is_device_ptr(cone_pix) || !is_device_ptr(r_lo) || !is_device_ptr(r_hi) || !is_device_ptr(shell_off_out))
+        return set_err(c, ISW_EINVAL, "cone_pix, r_lo, r_hi and shell_off_out must be device pointers");
+    if (n > 0 && (ld_out < n || !is_device_ptr(samples_out)))
+        return set_err(c, ISW_EINVAL, "samples_out: device, ld_out >= n");
+    if ((r = set_device(c))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *src[1] = {shell_off};
+    const size_t bytes[1] = {(size_t)(nshell + 1) * 8};
+    void *dst[1];
+    if ((r = upload_meta(c, s, src, bytes, 1, dst))) return r;
+    const int64_t nb = cone_cut_scratch_blocks(n);
+    const size_t incl_bytes = ((size_t)(n > 0 ? n : 1) * 4 + 255) / 256 * 256;
+    if ((r = ensure_ws(c, kWsCut, incl_bytes + (size_t)(nb + 2) * 8))) return r;
+    int32_t *incl = (int32_t *)c->ws[kWsCut];
+    int64_t *block_tot = (int64_t *)((unsigned char *)c->ws[kWsCut] + incl_bytes);
+    int64_t *d_count = block_tot + nb + 1;
+    const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
+    launch_cone_cut(samples, ld, n, (const int64_t *)dst[0], nshell, nside_hz, cone_pix, r_lo, r_hi, xo[0], xo[1],
+                    xo[2], incl, block_tot, samples_out, ld_out, shell_off_out, d_count, s);
+    c->n_launch += n > 0 ? 4 : 2;
+    if ((r = check_launch(c, "cone_cut launch"))) return r;
+    if (count) {
+        cudaError_t e = cudaMemcpyAsync(count, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_err(c, e, "cone_cut count");
+    }
+    return ISW_OK;
 }
 
 int isw_map(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list, const double *samples,

@@ -30,6 +30,18 @@ void launch_lightcone_adjoint(int mode, const double *nodes, int64_t n, int64_t 
                               const double *gs, int64_t ldgs, int ngs, double *gn, int64_t ldgn, double *gl,
                               int64_t ldgl, int *runs, int64_t *first, int64_t *last, DevStatus *st, cudaStream_t s);
 
+// cone.cu: stacking with HEALPix cones
+void launch_vec2pix(int64_t N, const double *v, int64_t n, int64_t ld, int64_t *pix, DevStatus *st, cudaStream_t s);
+void launch_box_place(const double *nodes, int64_t ld, const int64_t *off_out, const int64_t *src_start,
+                      int64_t nshell, const double *place, double *out, int64_t ld_out, int64_t n_out,
+                      cudaStream_t s);
+// scratch: incl int32[n], block_tot int64[cone_cut_scratch_blocks(n) + 1]
+int64_t cone_cut_scratch_blocks(int64_t n);
+void launch_cone_cut(const double *S, int64_t ld, int64_t n, const int64_t *off, int64_t nshell, int64_t nside_hz,
+                     const int64_t *cone_pix, const double *r_lo, const double *r_hi, double xo0, double xo1,
+                     double xo2, int32_t *incl, int64_t *block_tot, double *out, int64_t ld_out, int64_t *off_out,
+                     int64_t *count, cudaStream_t s);
+
 // pack.cu: per-sample records of the map kernels and per-tile caps
 // far (may be NULL): far-field records for the FP32 pair kernel, pair-interleaved (n_pad even)
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,

@@ -17,3 +17,4 @@ from .strings import (  # noqa: F401
     config,
     CONFIG_NAMES,
 )
+from .stacking import StackWorkload, base_pixel_centres, stack_config  # noqa: F401
