@@ -88,6 +88,10 @@ def lib():
             L.or_cone_cut.argtypes = [_dp, ctypes.c_int64, _i64p, ctypes.c_int64, ctypes.c_int64, _i64p, _dp,
                                       _dp, _dp, _dp, ctypes.c_int64, _i64p]
             L.or_cone_cut.restype = ctypes.c_int64
+            L.or_isw_map_patch.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                           _dp, ctypes.c_int64, ctypes.c_int64, _dp, ctypes.c_double, ctypes.c_int,
+                                           _dp]
+            L.or_isw_map_patch.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -346,3 +350,35 @@ def cone_cut(samples, shell_off, nside_hz, cone_pix, r_lo, r_hi, x_obs=(0.0, 0.0
     if m < 0:
         raise ValueError("or_cone_cut failed")
     return out[:, :m], off
+
+
+FULLSKY, FLATSKY = 0, 1
+
+
+def isw_map_patch(frame, M: int, width: float, samples, approx: int = FULLSKY, x_obs=(0.0, 0.0, 0.0),
+                  GU: float = 1.0, rows=None, threads: int = 1):
+    """Theta on an M x M gnomonic patch (frame rows e1, e2, e3; coordinate width ``width``),
+    full sky (approx 0) or flat sky (approx 1): returns [M, M] (row j, column i), or only the
+    rows in ``rows`` = (j0, j1) (other rows zero)."""
+    frame = _c64(np.asarray(frame, dtype=np.float64).reshape(9))
+    samples = _c64(samples)
+    n = samples.shape[1]
+    j0, j1 = (0, M) if rows is None else rows
+    theta = np.zeros(M * M)
+    L = lib()
+    errors = []
+
+    def work(a, b):
+        r = L.or_isw_map_patch(_d(frame), M, float(width), j0 + a, j0 + b, _d(samples), n, n, _d(_c64(x_obs)),
+                               float(GU), int(approx), _d(theta))
+        if r:
+            errors.append(r)
+
+    ths = [threading.Thread(target=work, args=r) for r in _split(j1 - j0, threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    if errors:
+        raise ValueError(f"or_isw_map_patch failed with status {errors[0]}")
+    return theta.reshape(M, M)

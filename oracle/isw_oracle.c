@@ -22,6 +22,8 @@
  *      condition): gradients of LINEAR box-time nodes and of BURDEN loop parameters
  *   8. stacking with HEALPix cones (Sec. III.B): own atan2, RING vec2pix, box placement,
  *      cone cut
+ *   9. patch maps: full sky on a gnomonic patch and the flat-sky approximation (Sec. II.A,
+ *      Fig. 3)
  *
  * Pins (tests/test_oracle_*.py) tie each part to something other than itself; see the
  * header comment of each section for what pins it.
@@ -959,4 +961,108 @@ int64_t or_cone_cut(const double *samples, int64_t ld, const int64_t *shell_off,
         shell_off_out[k + 1] = o;
     }
     return o;
+}
+
+/* ------------------------------------------------------------------------------------
+ * 9. Patch maps: full sky vs the flat-sky / small-angle approximation (Sec. II.A: the limit
+ * X n -> X with parallel photon paths; Sec. IV, Fig. 3: a gnomonic patch of the full-sky map
+ * against the flat-sky map of the same strings).
+ *
+ * Patch: orthonormal frame (e1, e2, e3) with e3 the patch centre; an M x M grid of gnomonic
+ * coordinates xi_i = (i + 1/2 - M/2) w/M, eta_j likewise (w the coordinate width); pixel
+ * (i, j) is stored at theta[j M + i].
+ *   full sky: the discrete Eq. (1) sum at n = (xi e1 + eta e2 + e3) / |xi e1 + eta e2 + e3|;
+ *   flat sky: every sample at depth Z = (X - x_obs).e3 > 0 sits at (xi_s, eta_s) =
+ *     ((X - x_obs).e1, (X - x_obs).e2) / Z and contributes
+ *       -4 GU eps dsigma / Z * (u_perp . d) / |d|^2,   d = (xi - xi_s, eta - eta_s),
+ *     with u = Xdot - (e3.X') X' / (1 + e3.Xdot) (the photon direction fixed to e3) and
+ *     u_perp = (u.e1, u.e2); samples with Z <= 0 are skipped, d = 0 gives 0.
+ * Neumaier sums in input order.  Pinned by the flat-sky Kaiser-Stebbins step of a straight
+ * moving segment, -8 GU gamma v atan(Lambda / eta) at its midpoint, and by the approach of the
+ * full-sky patch to the flat-sky one at the centre of a small patch.
+ * ---------------------------------------------------------------------------------- */
+static void patch_dir(const double frame[9], int64_t M, double width, int64_t i, int64_t j,
+                      double *xi, double *eta, double n[3])
+{
+    double h = width / (double)M;
+    *xi = ((double)i + 0.5 - 0.5 * (double)M) * h;
+    *eta = ((double)j + 0.5 - 0.5 * (double)M) * h;
+    double v[3];
+    for (int k = 0; k < 3; ++k) v[k] = (*xi * frame[k] + *eta * frame[3 + k]) + frame[6 + k];
+    double r = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    for (int k = 0; k < 3; ++k) n[k] = v[k] / r;
+}
+
+/* rows j0 .. j1-1 of the patch; approx 0 = full sky, 1 = flat sky */
+int or_isw_map_patch(const double frame[9], int64_t M, double width, int64_t j0, int64_t j1,
+                     const double *samples, int64_t n, int64_t ld, const double x_obs[3], double GU,
+                     int approx, double *theta)
+{
+    if (M < 1 || !(width > 0.0) || j0 < 0 || j1 > M) return OR_EINVAL;
+    if (approx == 0) {
+        seg_t *segs = (seg_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(seg_t));
+        if (!segs) return OR_EINVAL;
+        for (int64_t s = 0; s < n; ++s) seg_prepare(samples, ld, s, x_obs, GU, &segs[s]);
+        for (int64_t j = j0; j < j1; ++j)
+            for (int64_t i = 0; i < M; ++i) {
+                double xi, eta, nv[3];
+                patch_dir(frame, M, width, i, j, &xi, &eta, nv);
+                double sum = 0.0, comp = 0.0;
+                for (int64_t s = 0; s < n; ++s) {
+                    pair_t q;
+                    if (!segs[s].ok || !pair_eval(nv, &segs[s], &q)) continue;
+                    neumaier(&sum, &comp, segs[s].kappa * (q.uD / q.D2));
+                }
+                theta[j * M + i] = sum + comp;
+            }
+        free(segs);
+        return OR_OK;
+    }
+    /* flat sky: per-sample position in the patch and weight */
+    double *rec = (double *)malloc((size_t)(n > 0 ? n : 1) * 5 * sizeof(double));
+    int *ok = (int *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+    if (!rec || !ok) {
+        free(rec);
+        free(ok);
+        return OR_EINVAL;
+    }
+    for (int64_t s = 0; s < n; ++s) {
+        double r[3], Xd[3], Xp[3];
+        for (int k = 0; k < 3; ++k) {
+            r[k] = samples[k * ld + s] - x_obs[k];
+            Xd[k] = samples[(3 + k) * ld + s];
+            Xp[k] = samples[(6 + k) * ld + s];
+        }
+        double Z = dot3(r, frame + 6);
+        double v2 = dot3(Xd, Xd), xp2 = dot3(Xp, Xp);
+        double om = 1.0 - v2;
+        double eps = sqrt(xp2 / om);
+        double Bz = 1.0 + dot3(frame + 6, Xd), Az = dot3(frame + 6, Xp);
+        double u[3];
+        for (int k = 0; k < 3; ++k) u[k] = Xd[k] - (Az * Xp[k]) / Bz;
+        double kd = -4.0 * GU * (eps * samples[9 * ld + s]) / Z;
+        ok[s] = Z > 0.0 && om > 0.0 && Bz > 0.0 && isfinite(kd);
+        rec[5 * s + 0] = dot3(r, frame) / Z;
+        rec[5 * s + 1] = dot3(r, frame + 3) / Z;
+        rec[5 * s + 2] = kd * dot3(u, frame);
+        rec[5 * s + 3] = kd * dot3(u, frame + 3);
+        rec[5 * s + 4] = kd;
+    }
+    for (int64_t j = j0; j < j1; ++j)
+        for (int64_t i = 0; i < M; ++i) {
+            double xi, eta, nv[3];
+            patch_dir(frame, M, width, i, j, &xi, &eta, nv);
+            double sum = 0.0, comp = 0.0;
+            for (int64_t s = 0; s < n; ++s) {
+                if (!ok[s]) continue;
+                double dx = xi - rec[5 * s], dy = eta - rec[5 * s + 1];
+                double Q = dx * dx + dy * dy;
+                if (Q == 0.0) continue;
+                neumaier(&sum, &comp, (rec[5 * s + 2] * dx + rec[5 * s + 3] * dy) / Q);
+            }
+            theta[j * M + i] = sum + comp;
+        }
+    free(rec);
+    free(ok);
+    return OR_OK;
 }
