@@ -58,6 +58,8 @@ typedef enum {
 enum { ISW_F64 = 0, ISW_F32C = 1 };
 /* light-cone solve mode */
 enum { ISW_LINEAR = 0, ISW_BURDEN = 1 };
+/* patch maps: full-sky formula or the flat-sky / small-angle approximation */
+enum { ISW_FULLSKY = 0, ISW_FLATSKY = 1 };
 /* isw_map_batched flags */
 enum { ISW_SKIP_LIGHTCONE = 1, ISW_GRAPH = 2, ISW_AUTOTUNE = 4 };
 /* isw_set_param keys */
@@ -208,6 +210,26 @@ int cone_cut(isw_ctx *ctx, const double *samples, int64_t ld, const int64_t *she
 int isw_map(isw_ctx *ctx, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list,
             const double *samples, int64_t n, int64_t ld, const double *x_obs, double GU, int prec,
             int accumulate, double *theta_out, void *stream);
+
+/* A gnomonic patch map (Sec. IV, Fig. 3: full sky against the flat-sky / small-angle
+ * approximation on the same patch).
+ *   frame    : host double[9], orthonormal e1, e2, e3 (e3 = patch centre)
+ *   M, width : M x M pixels of gnomonic coordinates xi, eta in [-width/2, width/2]; pixel
+ *              (i, j) is centred at xi = (i + 1/2 - M/2) width/M, eta likewise, and stored at
+ *              theta_out[j M + i] (device double[M*M])
+ *   approx   : ISW_FULLSKY: the map of Eq. (1)-(2) at the directions (xi e1 + eta e2 + e3)/norm
+ *              (the isw_map kernels, prec as there); ISW_FLATSKY: the limit X n -> X with
+ *              parallel photon paths (Sec. II.A): a sample at depth Z = (X - x_obs).e3 > 0 sits
+ *              at ((X - x_obs).e1, (X - x_obs).e2)/Z and contributes
+ *              -4 GU eps dsigma / Z (u_perp . d)/|d|^2 with u = Xdot - (e3.X')X'/(1 + e3.Xdot),
+ *              u_perp its e1, e2 components and d the coordinate separation; samples with Z <= 0
+ *              contribute nothing, d = 0 gives 0.  ISW_F32C forms d from float-pair positions and
+ *              sums with compensation; ISW_F64 is plain FP64.
+ *   accumulate : 0 writes theta_out, 1 adds to it
+ * ISW_EINVAL for a frame that is not orthonormal (to 1e-9), M outside [1, 2^20] or width <= 0. */
+int isw_map_patch(isw_ctx *ctx, const double *frame, int64_t M, double width, const double *samples, int64_t n,
+                  int64_t ld, const double *x_obs, double GU, int prec, int approx, int accumulate,
+                  double *theta_out, void *stream);
 
 /* Adjoint of isw_map with respect to the samples (an extension of the method: the
  * derivative of Eq. (1)-(2)).  Given g = dL/dTheta (device double[npix], same pixel

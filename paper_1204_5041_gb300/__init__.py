@@ -28,6 +28,7 @@ __all__ = [
 OK, EINVAL, ECUDA, EDOMAIN, ENOCONV, ETIMEOUT, ENOMEM = range(7)
 F64, F32C = 0, 1
 LINEAR, BURDEN = 0, 1
+FULLSKY, FLATSKY = 0, 1
 SKIP_LIGHTCONE, GRAPH, AUTOTUNE = 1, 2, 4
 PARAM_NEAR_K, PARAM_B_MIN, PARAM_SPLIT, PARAM_VARIANT, PARAM_TIMING, PARAM_D_FAR = range(6)
 _STATUS_NAMES = {0: "ISW_OK", 1: "ISW_EINVAL", 2: "ISW_ECUDA", 3: "ISW_EDOMAIN", 4: "ISW_ENOCONV",
@@ -84,6 +85,8 @@ def lib():
                 "box_place": (_i32, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp, _i64, _vp, _vp]),
                 "cone_cut": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp,
                                     ctypes.POINTER(_i64), _vp]),
+                "isw_map_patch": (_i32, [_vp, _vp, _i64, _dbl, _vp, _i64, _i64, _vp, _dbl, _i32, _i32, _i32, _vp,
+                                         _vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -529,3 +532,24 @@ def isw_map_stacked(nside: int, nodes_box, box_off, shell_box, place, t_box, nsi
     kept, _ = cone_cut(samples, off, nside_hz, cone_pix, r_lo, r_hi, x_obs=x_obs, ctx=ctx, stream=stream)
     theta = isw_map(nside, kept, x_obs=x_obs, GU=GU, prec=prec, out=out, ctx=ctx, stream=stream)
     return theta, kept
+
+
+def isw_map_patch(frame, M: int, width: float, samples, approx: int = FULLSKY, x_obs=None, GU: float = 1.0,
+                  prec="f32c", accumulate: bool = False, out=None, ctx=None, stream=None):
+    """Theta on an M x M gnomonic patch (frame rows e1, e2, e3 with e3 the centre; gnomonic
+    coordinate width ``width``), full sky or flat sky: float64 CUDA tensor [M, M] (row j = eta)."""
+    import numpy as np
+
+    c = _ctx(ctx)
+    fr = np.ascontiguousarray(np.asarray(frame, dtype=np.float64).reshape(9))
+    _dev_tensor(samples, torch.float64, "samples")
+    n, ld = _rows(samples, 10, "samples")
+    if out is None:
+        out = torch.empty((M, M), dtype=torch.float64, device=samples.device)
+    _dev_tensor(out, torch.float64, "out")
+    if out.numel() != M * M or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 tensor of M*M elements")
+    c.check(lib().isw_map_patch(c.handle, fr.ctypes.data_as(_vp), int(M), float(width), _ptr(samples), n, ld,
+                                _xobs(x_obs), float(GU), _precision(prec), int(approx), int(bool(accumulate)),
+                                _ptr(out), _stream(stream)))
+    return out

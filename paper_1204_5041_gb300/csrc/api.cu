@@ -15,7 +15,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsFlat, kWsCount
 };
 static_assert(kWsCount <= kMaxWorkspaces, "isw_ctx holds kMaxWorkspaces workspace slots");
 
@@ -183,7 +183,7 @@ void timing_end(isw_ctx *c, int k, cudaStream_t s)
 // Shared body of isw_map: pixel table, sample records, caps, map kernel, partial reduce.
 int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list, const double *samples,
              int64_t n, int64_t ld, const double *x_obs, double GU, int prec, int accumulate, double *theta,
-             cudaStream_t s, int64_t tune_waves = 0, int64_t *tuned_pixels = nullptr)
+             cudaStream_t s, int64_t tune_waves = 0, int64_t *tuned_pixels = nullptr, const PatchSpec *patch = nullptr)
 {
     const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
     if (npix == 0) return ISW_OK;
@@ -202,7 +202,12 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     if (prec == ISW_F32C && !c->capturing) c->last_variant = vidx;
     const Variant v = prec == ISW_F32C ? f32_variant(vidx) : f64_variant();
     const int S = v.seg_tile;
-    const PixelPlan pp = plan_pixels(nside, pix0, npix, pix_list, v);
+    PixelPlan pp = plan_pixels(nside, pix0, npix, pix_list, v);
+    if (patch) {
+        pp.mode = 3;
+        pp.ntiles = ((patch->M + v.tx - 1) / v.tx) * ((patch->M + v.ty - 1) / v.ty);
+        pp.tot = pp.ntiles * v.tx * v.ty;
+    }
     const int64_t n_pad = (n + S - 1) / S * S;
     const int64_t nst = n_pad / S;
     const int slots = prec == ISW_F32C ? map_f32c_slots(vidx, c->num_sms) : map_f64_slots(c->num_sms);
@@ -218,7 +223,8 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     if (split > 1 && (r = ensure_ws(c, kWsPartial, (size_t)split * pp.tot * sizeof(double)))) return r;
     if ((r = ensure_ws(c, kWsQueue, 2 * sizeof(unsigned long long)))) return r;
 
-    const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
+    const double theta_pix = patch ? patch->width / (double)patch->M
+                                   : std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     double *nv = (double *)c->ws[kWsNv];
     int64_t *outidx = (int64_t *)c->ws[kWsOut];
     float4 *pcaps = (float4 *)c->ws[kWsPcap];
@@ -226,8 +232,9 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     Seg64 *s64 = (Seg64 *)c->ws[kWsS64];
     SegCap *scaps = (SegCap *)c->ws[kWsScap];
 
-    launch_pixel_table(nside, pp.mode, pix0, npix, pix_list, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx, pcaps,
-                       c->d_status, s);
+    if (patch) launch_patch_table(*patch, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx, pcaps, s);
+    else launch_pixel_table(nside, pp.mode, pix0, npix, pix_list, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx,
+                            pcaps, c->d_status, s);
     Far2 *far = prec == ISW_F32C ? (Far2 *)c->ws[kWsFar] : nullptr;
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, far, c->d_status, s);
     c->n_launch += 3;
@@ -675,6 +682,88 @@ int cone_cut(isw_ctx *c, const double *samples, int64_t ld, const int64_t *shell
         if (e != cudaSuccess) return cuda_err(c, e, "cone_cut count");
     }
     return ISW_OK;
+}
+
+int isw_map_patch(isw_ctx *c, const double *frame, int64_t M, double width, const double *samples, int64_t n,
+                  int64_t ld, const double *x_obs, double GU, int prec, int approx, int accumulate, double *theta_out,
+                  void *stream)
+{
+    if (!c) return ISW_EINVAL;
+    if (!frame) return set_err(c, ISW_EINVAL, "frame (host double[9]) is required");
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double d = frame[3 * a] * frame[3 * b] + frame[3 * a + 1] * frame[3 * b + 1] +
+                             frame[3 * a + 2] * frame[3 * b + 2];
+            if (!(std::fabs(d - (a == b ? 1.0 : 0.0)) < 1e-9)) return set_err(c, ISW_EINVAL, "frame is not orthonormal");
+        }
+    if (M < 1 || M > (1 << 20)) return set_err(c, ISW_EINVAL, "M out of range");
+    if (!(width > 0.0) || !std::isfinite(width)) return set_err(c, ISW_EINVAL, "width must be positive");
+    if (prec != ISW_F64 && prec != ISW_F32C) return set_err(c, ISW_EINVAL, "unknown precision %d", prec);
+    if (approx != ISW_FULLSKY && approx != ISW_FLATSKY) return set_err(c, ISW_EINVAL, "unknown approximation %d", approx);
+    int r;
+    if ((r = check_samples(c, samples, n, ld))) return r;
+    if (!is_device_ptr(theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
+    if (!std::isfinite(GU)) return set_err(c, ISW_EINVAL, "GU not finite");
+    if ((r = set_device(c))) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    PatchSpec p;
+    for (int k = 0; k < 9; ++k) p.frame[k] = frame[k];
+    p.M = M;
+    p.width = width;
+    const int64_t npix = M * M;
+    if (approx == ISW_FULLSKY)
+        return map_impl(c, 0, 0, npix, nullptr, samples, n, ld, x_obs, GU, prec, accumulate, theta_out, s, 0, nullptr,
+                        &p);
+    if (n == 0) {
+        if (!accumulate) {
+            cudaError_t e = cudaMemsetAsync(theta_out, 0, (size_t)npix * sizeof(double), s);
+            if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync");
+        }
+        return ISW_OK;
+    }
+    const bool f64 = prec == ISW_F64;
+    const int S = flat_seg_tile(), tx = flat_tx(), ty = flat_ty();
+    const int64_t ntiles = ((M + tx - 1) / tx) * ((M + ty - 1) / ty), tot = ntiles * tx * ty;
+    const int64_t n_pad = (n + S - 1) / S * S, nst = n_pad / S;
+    const int slots = flat_slots(f64, c->num_sms);
+    const int split = c->split_override > 0 ? c->split_override : choose_split(ntiles, nst, slots);
+    if ((r = ensure_ws(c, kWsNv, (size_t)tot * 3 * sizeof(double)))) return r;
+    if ((r = ensure_ws(c, kWsOut, (size_t)tot * sizeof(int64_t)))) return r;
+    if ((r = ensure_ws(c, kWsPcap, (size_t)ntiles * sizeof(float4)))) return r;
+    if ((r = ensure_ws(c, kWsFlat, (size_t)n_pad * flat_record_bytes()))) return r;
+    if ((r = ensure_ws(c, kWsQueue, 2 * sizeof(unsigned long long)))) return r;
+    if (split > 1 && (r = ensure_ws(c, kWsPartial, (size_t)split * tot * sizeof(double)))) return r;
+    double *nv = (double *)c->ws[kWsNv];
+    int64_t *outidx = (int64_t *)c->ws[kWsOut];
+    unsigned char *rec = (unsigned char *)c->ws[kWsFlat];
+    void *r32 = rec, *r64 = rec + (size_t)n_pad * (flat_record_bytes() / 2);
+    unsigned long long *queue = (unsigned long long *)c->ws[kWsQueue];
+    const double xo[3] = {x_obs ? x_obs[0] : 0.0, x_obs ? x_obs[1] : 0.0, x_obs ? x_obs[2] : 0.0};
+    launch_patch_table(p, tx, ty, ntiles, nv, tot, outidx, (float4 *)c->ws[kWsPcap], s);
+    launch_flat_pack(samples, n, ld, p, xo[0], xo[1], xo[2], GU, n_pad, r32, r64, s);
+    c->n_launch += 3;
+    const int64_t items = ntiles * split;
+    const int grid = (int)(items < slots ? items : slots);
+    const int ti = timing_begin(c, s);
+    cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync(work counters)");
+    launch_map_flat(f64, r32, r64, outidx, ntiles, nst, split, M, width / (double)M, theta_out,
+                    split > 1 ? (double *)c->ws[kWsPartial] : nullptr, accumulate, c->d_status, queue, grid, s);
+    c->n_launch += 1;
+    c->n_pair += 1;
+    if (split > 1) {
+        MapArgs a{};
+        a.outidx = outidx;
+        a.ntiles = ntiles;
+        a.split = split;
+        a.theta = theta_out;
+        a.partial = (double *)c->ws[kWsPartial];
+        a.accumulate = accumulate;
+        launch_reduce_partials(a, tx * ty, s);
+        c->n_launch += 1;
+    }
+    timing_end(c, ti, s);
+    return check_launch(c, "isw_map_patch launch");
 }
 
 int isw_map(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list, const double *samples,

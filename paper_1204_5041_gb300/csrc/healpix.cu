@@ -119,6 +119,46 @@ __global__ void k_pixel_caps(const double *__restrict__ nv, int64_t ldn, const i
     }
 }
 
+// Patch table: tile t is block (t mod ntx, t / ntx) of tx x ty pixels of the M x M grid;
+// padding slots hold the patch centre with output index -1.
+__global__ void k_patch_table(PatchSpec p, int tx, int ty, int64_t ntiles, double *__restrict__ nv, int64_t ldn,
+                              int64_t *__restrict__ outidx)
+{
+    const int tile_sz = tx * ty;
+    const int64_t total = ntiles * tile_sz;
+    const int64_t ntx = (p.M + tx - 1) / tx;
+    const double h = p.width / (double)p.M;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = k / tile_sz;
+        const int l = (int)(k - t * tile_sz);
+        const int64_t i = (t % ntx) * tx + (l % tx), j = (t / ntx) * ty + (l / tx);
+        double v[3] = {p.frame[6], p.frame[7], p.frame[8]};
+        int64_t oi = -1;
+        if (i < p.M && j < p.M) {
+            const double xi = ((double)i + 0.5 - 0.5 * (double)p.M) * h;
+            const double eta = ((double)j + 0.5 - 0.5 * (double)p.M) * h;
+            for (int c = 0; c < 3; ++c) v[c] = xi * p.frame[c] + eta * p.frame[3 + c] + p.frame[6 + c];
+            const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            for (int c = 0; c < 3; ++c) v[c] /= r;
+            oi = j * p.M + i;
+        }
+        nv[k] = v[0];
+        nv[ldn + k] = v[1];
+        nv[2 * ldn + k] = v[2];
+        outidx[k] = oi;
+    }
+}
+
+void launch_patch_table(const PatchSpec &p, int tx, int ty, int64_t ntiles, double *nv, int64_t ldn,
+                        int64_t *outidx, float4 *caps, cudaStream_t s)
+{
+    const int64_t total = ntiles * tx * ty;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_patch_table<<<(unsigned)blocks, 256, 0, s>>>(p, tx, ty, ntiles, nv, ldn, outidx);
+    k_pixel_caps<<<(unsigned)ntiles, 256, 0, s>>>(nv, ldn, outidx, tx * ty, caps);
+}
+
 int launch_pix2vec(int64_t N, int64_t pix0, int64_t npix, const int64_t *pix_list, double *out, int64_t ld,
                    DevStatus *st, cudaStream_t s)
 {

@@ -12,6 +12,30 @@ void launch_pixel_table(int64_t N, int mode, int64_t pix0, int64_t npix, const i
                         int64_t ntiles, double *nv, int64_t ldn, int64_t *outidx, float4 *caps, DevStatus *st,
                         cudaStream_t s);
 
+// A gnomonic patch: orthonormal frame (e1, e2, e3) with e3 the centre, M x M pixels of
+// coordinate pitch width / M; pixel (i, j) at (xi, eta) = ((i + 1/2 - M/2), (j + 1/2 - M/2)) * pitch,
+// direction (xi e1 + eta e2 + e3) / norm, output slot j M + i.
+struct PatchSpec {
+    double frame[9];
+    int64_t M;
+    double width;
+};
+// patch pixel table: compact tx x ty blocks of the M x M grid (caps as for the sphere)
+void launch_patch_table(const PatchSpec &p, int tx, int ty, int64_t ntiles, double *nv, int64_t ldn,
+                        int64_t *outidx, float4 *caps, cudaStream_t s);
+
+// flat.cu: flat-sky patch map (pixel tiles 32 x flat_ty() of the patch table)
+int flat_seg_tile();
+int flat_tx();
+int flat_ty();
+size_t flat_record_bytes();   // FP32 + FP64 record bytes per sample
+int flat_slots(bool f64, int num_sms);
+void launch_flat_pack(const double *S, int64_t n, int64_t ld, const PatchSpec &p, double xo0, double xo1, double xo2,
+                      double GU, int64_t n_pad, void *r32, void *r64, cudaStream_t s);
+void launch_map_flat(bool f64, const void *r32, const void *r64, const int64_t *outidx, int64_t ntiles, int64_t nst,
+                     int split, int64_t M, double pitch, double *theta, double *partial, int accumulate,
+                     DevStatus *st, unsigned long long *queue, int grid, cudaStream_t s);
+
 // lightcone.cu
 void launch_lightcone(int mode, const double *nodes, int64_t n, int64_t ld, const double *P, int64_t nloops,
                       int64_t ldp, double t_box, double xo0, double xo1, double xo2, double t_obs, double tol,
