@@ -304,6 +304,62 @@ def run_gpu(args):
         extra["adjoint"] = {"workload": f"{w3.name}: Nside={w3.nside}, {w3.n:,} samples, dL/dX and dL/dXdot",
                             "value": w3.npix * w3.n / (ms3 / 1e3), "unit": UNIT, "ms": ms3,
                             "fp64_value": w3.npix * w3.n / (ms3_64 / 1e3), "fp64_ms": ms3_64}
+        # gradient through the light-cone solve: map adjoint with the dsigma row, then the
+        # loop-parameter chain (98 Burden loops)
+        tau3 = torch.empty(w3.n, dtype=torch.float64, device=dev)
+        s3 = isw.lightcone_intersect(isw.BURDEN, n3, l3, tau=tau3)
+        g10 = torch.empty((10, w3.n), dtype=torch.float64, device=dev)
+        ms_m10 = timed(lambda: isw.isw_map_adjoint(w3.nside, s3, g3, prec="f32c", ngrad=10, out=g10))
+        ms_lc = timed(lambda: isw.lightcone_adjoint(isw.BURDEN, n3, tau3, g10, loop_params=l3))
+        extra["adjoint"].update({"lightcone_adjoint_ms": ms_lc, "map_adjoint_10rows_ms": ms_m10,
+                                 "note": "lightcone_adjoint chains dL/d(samples) to the 98 loops' parameters"})
+        del n3, s3, g3, gout, g10
+        # stacking with HEALPix cones: 12 base-pixel cones from 4 boxes used 3 times each
+        wst = synth.stack_config(seed=args.seed, nside=512)
+        nb = torch.from_numpy(np.ascontiguousarray(wst.nodes_box)).to(dev)
+        plc = torch.from_numpy(np.ascontiguousarray(wst.place)).to(dev)
+        cpx = torch.from_numpy(wst.cone_pix).to(dev)
+        rlo, rhi = torch.from_numpy(wst.r_lo).to(dev), torch.from_numpy(wst.r_hi).to(dev)
+        run_st = lambda: isw.isw_map_stacked(wst.nside, nb, wst.box_off, wst.shell_box, plc, wst.t_box, wst.nside_hz,
+                                             cpx, rlo, rhi, prec="f32c")
+        _, kept = run_st()
+        ms_st = timed(run_st)
+        extra["stacked"] = {"workload": f"{wst.name}: 12 HEALPix cones (N_side^hz = 1) filled from 4 boxes used 3 "
+                                        f"times, {wst.n_placed:,} placed nodes, {kept.shape[1]:,} kept; Nside={wst.nside}",
+                            "value": wst.npix * kept.shape[1] / (ms_st / 1e3), "unit": UNIT, "ms": ms_st,
+                            "note": "box_place + light-cone solve + cone cut (one host sync) + map; pairs of kept samples"}
+        del nb, kept
+        # full sky vs flat sky on a 7.2-degree gnomonic patch of the bench network (Fig. 3)
+        lin_mean = w.nodes[0:3, w.shell_off[1]:].mean(axis=1)
+        e3 = lin_mean / np.linalg.norm(lin_mean)
+        e1 = np.cross([0.0, 0.0, 1.0], e3)
+        e1 /= np.linalg.norm(e1)
+        frame = np.stack([e1, np.cross(e3, e1), e3])
+        s1 = torch.empty((10, w.n), dtype=torch.float64, device=dev)
+        for k in range(w.nshell):
+            a0, a1 = int(w.shell_off[k]), int(w.shell_off[k + 1])
+            isw.lightcone_intersect(int(w.mode[k]), nodes_d[:, a0:a1], loops_d, t_box=float(w.t_box[k]),
+                                    x_obs=w.x_obs, t_obs=w.t_obs, out=s1[:, a0:a1])
+        Mp, wp = 1024, float(np.deg2rad(7.2))
+        full = isw.isw_map_patch(frame, Mp, wp, s1, approx=isw.FULLSKY)
+        flat = isw.isw_map_patch(frame, Mp, wp, s1, approx=isw.FLATSKY)
+        ms_full = timed(lambda: isw.isw_map_patch(frame, Mp, wp, s1, approx=isw.FULLSKY, out=full))
+        ms_flat = timed(lambda: isw.isw_map_patch(frame, Mp, wp, s1, approx=isw.FLATSKY, out=flat))
+        fh, fl = full.cpu().numpy(), flat.cpu().numpy()
+        fh, fl = fh - fh.mean(), fl - fl.mean()
+        yy, xx = np.mgrid[0:Mp, 0:Mp]
+        rad = np.hypot(xx - (Mp - 1) / 2, yy - (Mp - 1) / 2) / (Mp / 2)
+        rms_full = float(np.sqrt(np.mean(fh ** 2)))
+        diff = lambda m: float(np.sqrt(np.mean((fh[m] - fl[m]) ** 2)) / rms_full)
+        nf = int(s1.shape[1])
+        extra["patch"] = {"workload": f"7.2-degree gnomonic patch, {Mp}x{Mp} pixels, {nf:,} samples of {w.name}; "
+                                      f"full sky vs flat sky, each map's mean removed for the comparison",
+                          "full_value": Mp * Mp * nf / (ms_full / 1e3), "full_ms": ms_full,
+                          "flat_value": Mp * Mp * nf / (ms_flat / 1e3), "flat_ms": ms_flat, "unit": UNIT,
+                          "rms_full_minus_flat_over_rms": {"centre_r<0.25": diff(rad < 0.25),
+                                                           "ring_0.75<r<1": diff((rad > 0.75) & (rad < 1.0)),
+                                                           "all": diff(rad >= 0)}}
+        del s1, full, flat
         r, _ = ctx.check_status()
         if r != isw.OK:
             raise RuntimeError(f"device status {r} in the extra measurements: {ctx.last_error()}")
