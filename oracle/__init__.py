@@ -92,6 +92,12 @@ def lib():
                                            _dp, ctypes.c_int64, ctypes.c_int64, _dp, ctypes.c_double, ctypes.c_int,
                                            _dp]
             L.or_isw_map_patch.restype = ctypes.c_int
+            L.or_map_alm_cl.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, _dp, _dp]
+            L.or_map_alm_cl.restype = ctypes.c_int
+            L.or_ring_info.argtypes = [ctypes.c_int64, ctypes.c_int64, _dp, _i64p, _i64p, _dp]
+            L.or_ring_info.restype = None
+            L.or_legendre_column.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _dp]
+            L.or_legendre_column.restype = None
             _lib = L
     return _lib
 
@@ -382,3 +388,32 @@ def isw_map_patch(frame, M: int, width: float, samples, approx: int = FULLSKY, x
     if errors:
         raise ValueError(f"or_isw_map_patch failed with status {errors[0]}")
     return theta.reshape(M, M)
+
+
+def map_alm_cl(nside: int, theta, lmax: int):
+    """Spherical-harmonic analysis of a full-sky RING map: returns (alm complex [mmax+1, lmax+1],
+    only l >= m filled; cl [lmax+1])."""
+    theta = _c64(theta)
+    assert theta.size == 12 * nside * nside
+    alm = np.zeros(2 * (lmax + 1) * (lmax + 1))
+    cl = np.zeros(lmax + 1)
+    r = lib().or_map_alm_cl(int(nside), _d(theta), int(lmax), _d(alm), _d(cl))
+    if r:
+        raise ValueError(f"or_map_alm_cl failed with status {r}")
+    a = alm.reshape(2, lmax + 1, lmax + 1)
+    return a[0] + 1j * a[1], cl
+
+
+def ring_info(nside: int, i: int):
+    """(z, pixels, first pixel, phi_0 in turns) of RING ring i (1 .. 4N-1) as the analysis uses it."""
+    z, t0 = ctypes.c_double(), ctypes.c_double()
+    npx, p0 = ctypes.c_int64(), ctypes.c_int64()
+    lib().or_ring_info(int(nside), int(i), ctypes.byref(z), ctypes.byref(npx), ctypes.byref(p0), ctypes.byref(t0))
+    return z.value, npx.value, p0.value, t0.value
+
+
+def legendre_column(z: float, m: int, lmax: int):
+    """Normalised associated Legendre values lambda_lm(z), l = 0 .. lmax (zero for l < m)."""
+    out = np.zeros(lmax + 1)
+    lib().or_legendre_column(float(z), int(m), int(lmax), _d(out))
+    return out
