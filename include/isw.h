@@ -231,6 +231,19 @@ int isw_map_patch(isw_ctx *ctx, const double *frame, int64_t M, double width, co
                   int64_t ld, const double *x_obs, double GU, int prec, int approx, int accumulate,
                   double *theta_out, void *stream);
 
+/* Angular power spectrum of a full-sky RING map (Sec. IV, Fig. 4): spherical-harmonic analysis
+ * with uniform pixel weights, a_lm = (4 pi / N_pix) sum_p Theta_p conj(Y_lm(n_p)) (Condon-Shortley
+ * phase), C_l = (|a_l0|^2 + 2 sum_{m>=1} |a_lm|^2) / (2l + 1).
+ *   theta : device double[12 nside^2], RING order; nside <= 1024
+ *   lmax  : 0 .. 4 nside (m runs to lmax)
+ *   alm   : device double[2][lmax+1][lmax+1] (real plane, then imaginary; entry [m][l], zero for
+ *           l < m) or NULL (kept in the context's workspace)
+ *   cl    : device double[lmax+1]
+ * Per-ring Fourier sums cost N_pix (lmax + 1) complex products (no FFT); the sums over rings
+ * have a fixed order (deterministic). */
+int isw_map_cl(isw_ctx *ctx, int64_t nside, const double *theta, int64_t lmax, double *alm, double *cl,
+               void *stream);
+
 /* Adjoint of isw_map with respect to the samples (an extension of the method: the
  * derivative of Eq. (1)-(2)).  Given g = dL/dTheta (device double[npix], same pixel
  * selection), writes grad_out = device double[ngrad][ld_g] with rows dL/dX (3), dL/dXdot (3),

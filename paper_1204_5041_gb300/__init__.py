@@ -87,6 +87,7 @@ def lib():
                                     ctypes.POINTER(_i64), _vp]),
                 "isw_map_patch": (_i32, [_vp, _vp, _i64, _dbl, _vp, _i64, _i64, _vp, _dbl, _i32, _i32, _i32, _vp,
                                          _vp]),
+                "isw_map_cl": (_i32, [_vp, _i64, _vp, _i64, _vp, _vp, _vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -553,3 +554,18 @@ def isw_map_patch(frame, M: int, width: float, samples, approx: int = FULLSKY, x
                                 _xobs(x_obs), float(GU), _precision(prec), int(approx), int(bool(accumulate)),
                                 _ptr(out), _stream(stream)))
     return out
+
+
+def isw_map_cl(nside: int, theta, lmax: int, with_alm: bool = False, ctx=None, stream=None):
+    """Angular power spectrum of a full-sky RING map (float64 CUDA tensor [12 nside^2]): returns
+    cl [lmax + 1], or (alm complex [lmax + 1 (m), lmax + 1 (l)], cl) with ``with_alm``."""
+    c = _ctx(ctx)
+    _dev_tensor(theta, torch.float64, "theta")
+    if theta.numel() != 12 * nside * nside or not theta.is_contiguous():
+        raise ValueError("theta must be a contiguous full-sky RING map")
+    cl = torch.empty(lmax + 1, dtype=torch.float64, device=theta.device)
+    alm = torch.empty((2, lmax + 1, lmax + 1), dtype=torch.float64, device=theta.device) if with_alm else None
+    c.check(lib().isw_map_cl(c.handle, int(nside), _ptr(theta), int(lmax), _ptr(alm), _ptr(cl), _stream(stream)))
+    if with_alm:
+        return torch.complex(alm[0], alm[1]), cl
+    return cl

@@ -15,7 +15,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsFlat, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsFlat, kWsClF, kWsAlm, kWsCount
 };
 static_assert(kWsCount <= kMaxWorkspaces, "isw_ctx holds kMaxWorkspaces workspace slots");
 
@@ -764,6 +764,26 @@ int isw_map_patch(isw_ctx *c, const double *frame, int64_t M, double width, cons
     }
     timing_end(c, ti, s);
     return check_launch(c, "isw_map_patch launch");
+}
+
+int isw_map_cl(isw_ctx *c, int64_t nside, const double *theta, int64_t lmax, double *alm, double *cl, void *stream)
+{
+    if (!c) return ISW_EINVAL;
+    if (nside < 1 || nside > cl_max_nside()) return set_err(c, ISW_EINVAL, "nside must be in [1, %d]", cl_max_nside());
+    if (lmax < 0 || lmax > 4 * nside) return set_err(c, ISW_EINVAL, "lmax must be in [0, 4 nside]");
+    if (!is_device_ptr(theta) || !is_device_ptr(cl) || (alm && !is_device_ptr(alm)))
+        return set_err(c, ISW_EINVAL, "theta, cl (and alm when given) must be device pointers");
+    int r;
+    if ((r = set_device(c))) return r;
+    const size_t L1 = (size_t)lmax + 1;
+    if ((r = ensure_ws(c, kWsClF, 2 * (size_t)(4 * nside - 1) * L1 * sizeof(double)))) return r;
+    if (!alm) {
+        if ((r = ensure_ws(c, kWsAlm, 2 * L1 * L1 * sizeof(double)))) return r;
+        alm = (double *)c->ws[kWsAlm];
+    }
+    launch_map_cl(nside, theta, lmax, (double *)c->ws[kWsClF], alm, cl, (cudaStream_t)stream);
+    c->n_launch += 3;
+    return check_launch(c, "isw_map_cl launch");
 }
 
 int isw_map(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_t *pix_list, const double *samples,

@@ -36,6 +36,10 @@ void launch_map_flat(bool f64, const void *r32, const void *r64, const int64_t *
                      int split, int64_t M, double pitch, double *theta, double *partial, int accumulate,
                      DevStatus *st, unsigned long long *queue, int grid, cudaStream_t s);
 
+// cl.cu: angular power spectrum (F: double[2][4N-1][lmax+1] workspace; alm: double[2][lmax+1][lmax+1])
+int cl_max_nside();
+void launch_map_cl(int64_t N, const double *map, int64_t lmax, double *F, double *alm, double *cl, cudaStream_t s);
+
 // lightcone.cu
 void launch_lightcone(int mode, const double *nodes, int64_t n, int64_t ld, const double *P, int64_t nloops,
                       int64_t ldp, double t_box, double xo0, double xo1, double xo2, double t_obs, double tol,
