@@ -360,6 +360,15 @@ def run_gpu(args):
                                                            "ring_0.75<r<1": diff((rad > 0.75) & (rad < 1.0)),
                                                            "all": diff(rad >= 0)}}
         del s1, full, flat
+        # angular power spectrum of the bench map (Fig. 4): l_max = 3 N_side
+        lmax_cl = 3 * w.nside
+        cl_t = isw.isw_map_cl(w.nside, theta_d, lmax_cl)
+        ms_cl = timed(lambda: isw.isw_map_cl(w.nside, theta_d, lmax_cl))
+        clv = cl_t.cpu().numpy()
+        extra["cl"] = {"workload": f"C_l of the {w.name} map, l_max = {lmax_cl} (RING analysis, uniform weights)",
+                       "ms": ms_cl,
+                       "l(l+1)C_l/2pi": {str(l): float(l * (l + 1) * clv[l] / (2 * np.pi))
+                                         for l in (10, 100, 300, 600, 1000, 1500) if l <= lmax_cl}}
         r, _ = ctx.check_status()
         if r != isw.OK:
             raise RuntimeError(f"device status {r} in the extra measurements: {ctx.last_error()}")
