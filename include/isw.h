@@ -69,7 +69,8 @@ enum {
     ISW_PARAM_SPLIT = 2,
     ISW_PARAM_VARIANT = 3,
     ISW_PARAM_TIMING = 4,
-    ISW_PARAM_D_FAR = 5
+    ISW_PARAM_D_FAR = 5,
+    ISW_PARAM_NUM_VARIANTS = 6   /* read-only (isw_get_param): number of FP32 kernel variants */
 };
 
 /* Create a context bound to CUDA device `device`.  Allocates a small device status block.

@@ -30,7 +30,7 @@ F64, F32C = 0, 1
 LINEAR, BURDEN = 0, 1
 FULLSKY, FLATSKY = 0, 1
 SKIP_LIGHTCONE, GRAPH, AUTOTUNE = 1, 2, 4
-PARAM_NEAR_K, PARAM_B_MIN, PARAM_SPLIT, PARAM_VARIANT, PARAM_TIMING, PARAM_D_FAR = range(6)
+PARAM_NEAR_K, PARAM_B_MIN, PARAM_SPLIT, PARAM_VARIANT, PARAM_TIMING, PARAM_D_FAR, PARAM_NUM_VARIANTS = range(7)
 _STATUS_NAMES = {0: "ISW_OK", 1: "ISW_EINVAL", 2: "ISW_ECUDA", 3: "ISW_EDOMAIN", 4: "ISW_ENOCONV",
                  5: "ISW_ETIMEOUT", 6: "ISW_ENOMEM"}
 

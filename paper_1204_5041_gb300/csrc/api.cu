@@ -395,6 +395,7 @@ int isw_get_param(const isw_ctx *c, int key, double *value)
     case ISW_PARAM_VARIANT: *value = c->last_variant; return ISW_OK;
     case ISW_PARAM_TIMING: *value = c->timing; return ISW_OK;
     case ISW_PARAM_D_FAR: *value = c->d_far; return ISW_OK;
+    case ISW_PARAM_NUM_VARIANTS: *value = num_f32_variants(); return ISW_OK;
     default: return ISW_EINVAL;
     }
 }

@@ -40,7 +40,9 @@ def _err(got, ref):
 
 
 def isw_num_variants():
-    return 11
+    import paper_1204_5041_gb300 as m
+
+    return int(m.default_context().get_param(m.PARAM_NUM_VARIANTS))
 
 
 def _status_ok(isw):
