@@ -483,7 +483,7 @@ def box_place(nodes_box, box_off, shell_box, place, out=None, ctx=None, stream=N
     _dev_tensor(place, torch.float64, "place")
     if place.numel() != 12 * sbox.size or not place.is_contiguous():
         raise ValueError("place must be a contiguous float64 CUDA tensor [nshell, 12]")
-    n_out = int(sum(boff[b + 1] - boff[b] for b in sbox))
+    n_out = int(sum(boff[b + 1] - boff[b] for b in sbox if 0 <= b < boff.size - 1))   # bad ids: the call rejects
     if out is None:
         out = torch.empty((10, max(n_out, 1)), dtype=torch.float64, device=nodes_box.device)
     _, ld_out = _rows(out, 10, "out")
