@@ -215,16 +215,17 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
 #pragma unroll
                     for (int k = 0; k < kAcc; ++k) part[k] = 0.f;
                     if (far) {
-                        // |d| >= d_far here: d from the leading floats is accurate to ~1e-7
+                        // |d| >= d_far here: d from the leading floats is accurate to ~1e-7, and
+                        // Xdot.d = B - e, X'.d = A - f from the record's constants (their
+                        // cancellation costs at most a factor 1/|d| <= 4)
 #pragma unroll 2
                         for (int q = w0; q < w0 + 32; ++q) {
                             const float4 pa = sp[q].a;
                             const float dx = pa.x - r.a.x, dy = pa.y - r.a.y, dz = pa.z - r.a.z;
                             const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            const float Pd = fmaf(r.d.z, dz, fmaf(r.d.y, dy, r.d.x * dx));
-                            const float Qd = fmaf(r.e.z, dz, fmaf(r.e.y, dy, r.e.x * dx));
                             const float A = fmaf(pa.z, r.e.z, fmaf(pa.y, r.e.y, pa.x * r.e.x));
                             const float B = fmaf(pa.z, r.d.z, fmaf(pa.y, r.d.y, fmaf(pa.x, r.d.x, 1.f)));
+                            const float Pd = B - r.d.w, Qd = A - r.e.w;
                             adj_pair32<NG9>(dx, dy, dz, Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
                         }
                     } else {
