@@ -9,8 +9,10 @@ available, so every workload here is drawn from a PCG64 stream:
   offset t0.  The loop is stored as 17 parameters; its nodes carry (loop id, sigma).
 * Long strings: random-walk polylines with isotropic steps, node velocities
   orthogonal to the local tangent with |Xdot| ~ U[0.3, 0.85], X' along the tangent
-  with |Xdot|^2 + |X'|^2 = 1 and d(sigma) chosen so that eps * d(sigma) is the
-  node's share of polyline length (half the two adjacent steps, one step at ends).
+  with |Xdot|^2 + |X'|^2 = 1 (so eps = 1) and d(sigma) chosen so that the length
+  element |X'| d(sigma) is the node's share of the polyline (half of each adjacent
+  step; the end nodes get half a step); the weight eps d(sigma) is then gamma times
+  that share, the string's energy element.
 
 Units: flat conformal coordinates in horizon units; the observer sits at x_obs = 0
 at conformal time t_obs = 1.
