@@ -8,13 +8,16 @@
 * continuum limit: for a Burden loop the node sum converges spectrally to an mpmath
   quadrature over sigma of Eq. (1) with the retarded time solved at every sigma;
 * invariants: linearity in the sample set, proportionality to GU, permutation of the
-  samples, exact pixel permutations under a quarter turn about z and a half turn about x;
+  samples, exact pixel permutations under a quarter turn about z and a half turn about x,
+  scale invariance (X and dsigma scaled together; exact for a factor 2), translation of the
+  observer together with the samples;
 * special cases: D = 0 gives a zero term, |Xdot| >= 1 samples are skipped (both counted);
 * adjoint: central finite differences (h = 1e-6) of L = sum (Theta - Theta_t)^2.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 
@@ -271,3 +274,29 @@ def test_adjoint_vs_finite_differences(oracle_lib):
     for blk in (slice(0, 3), slice(3, 6), slice(6, 9)):
         scale = np.max(np.abs(an[blk]))
         assert np.max(np.abs(fd[blk] - an[blk])) <= 1e-6 * scale
+
+
+def test_scale_and_observer_translation():
+    """X -> lambda X with dsigma -> lambda dsigma leaves every term unchanged (the weight depends on
+    dsigma / |X|, the direction on X / |X|): exactly for lambda = 2, to rounding otherwise.  Moving
+    the observer and every sample by the same vector leaves the map unchanged (a use of |X| in
+    place of |X - x_obs| anywhere would break it)."""
+    w = synth.config(0, seed=6)
+    S, _, st = oracle.lightcone(oracle.BURDEN, w.nodes[:, :1024], w.loop_params)
+    assert np.all(st == 0)
+    N = 8
+    th, _ = oracle.isw_map(N, S)
+    for lam, exact in ((2.0, True), (2.5, False)):
+        T = S.copy()
+        T[0:3] *= lam
+        T[9] *= lam
+        th2, _ = oracle.isw_map(N, T)
+        if exact:
+            assert np.array_equal(th2, th)
+        else:
+            np.testing.assert_allclose(th2, th, rtol=0, atol=1e-13 * np.abs(th).max())
+    shift = np.array([0.3, -0.7, 0.45])
+    T = S.copy()
+    T[0:3] += shift[:, None]
+    th3, _ = oracle.isw_map(N, T, x_obs=shift)
+    np.testing.assert_allclose(th3, th, rtol=0, atol=1e-12 * np.abs(th).max())
