@@ -37,7 +37,10 @@ import synth  # noqa: E402
 METRIC = "pixel\u00b7segment pairs/s (FP32 vs FP64 GPU) and % FP32 peak, at stated max err"
 UNIT = "pairs/s"
 FLOPS_PER_PAIR = 36          # algorithmic flops of one Eq. (1)-(2) pair term, FMA = 2
-SM_COUNT, FP32_LANES = 152, 128
+# algorithmic flops of one pair of the adjoint (dL/dX, dL/dXdot: the derivative sums of
+# isw_map_adjoint in textbook form, FMA = 2, the two reciprocals not counted)
+ADJ_FLOPS_PER_PAIR = 66
+FP32_LANES = 128             # FP32 FMA lanes per SM (Blackwell)
 
 
 def _peaks():
@@ -48,10 +51,10 @@ def _peaks():
         return {}
 
 
-def fp32_peak_tflops():
+def fp32_peak_tflops(sm_count: int):
     """Dense FP32 peak from unit counts and the maximum SM clock: SMs x 128 lanes x 2 flop x clock."""
     mhz = _peaks().get("sm_max_mhz", 2070.0)
-    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12, mhz
+    return sm_count * FP32_LANES * 2 * mhz * 1e6 / 1e12, mhz
 
 
 def workload_config(w):
@@ -142,20 +145,32 @@ def kernel_sources_sha1() -> str:
     return h.hexdigest()
 
 
-def profiled_traffic(variant: int):
-    """DRAM bytes per step of the pair kernels from the committed ncu summary, when it was taken on
-    the current kernel sources and the same variant; else None."""
+def _profile_record(name: str, pattern: str, variant: int):
+    """A machine-readable figure of a committed ncu summary, when it was taken on the current
+    kernel sources and the same variant; else None."""
     import re
 
     try:
-        txt = open(os.path.join(ROOT, "profiles", "launches_nside512_200k_seg.md")).read()
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
     except OSError:
         return None
     sha = kernel_sources_sha1()
-    for tb, v, s in re.findall(r"traffic_bytes_per_step=(\d+) variant=(-?\d+) csrc_sha1=([0-9a-f]+)", txt):
+    for val, v, s in re.findall(pattern + r" variant=(-?\d+) csrc_sha1=([0-9a-f]+)", txt):
         if int(v) == variant and s == sha:
-            return int(tb)
+            return val
     return None
+
+
+def profiled_traffic(variant: int):
+    """DRAM bytes per step of the pair kernels (ncu launch list of the bench step)."""
+    v = _profile_record("launches_nside512_200k_seg.md", r"traffic_bytes_per_step=(\d+)", variant)
+    return int(v) if v is not None else None
+
+
+def profiled_fma_busy(variant: int):
+    """FMA-pipe busy fraction of the far-field pass (ncu capture of the bench workload)."""
+    v = _profile_record("pair_kernel_far_nside512.md", r"fma_pipe_busy=([0-9.]+)", variant)
+    return float(v) if v is not None else None
 
 
 def _dist():
@@ -266,12 +281,34 @@ def run_gpu(args):
         return a0.elapsed_time(a1)
 
     # ---- plain FP64 GPU path, one step (outside the timed region), for the FP32/FP64 ratio
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    # measured FMA-pipe peaks of this GPU (calibration kernels, outside the timed region)
+    fma32 = ctx.fma_rate("f32c") / 1e12
+    fma64 = ctx.fma_rate("f64") / 1e12
+
+    def timed_kernel(fn):
+        """(event time of fn on the stream, device time of its pair-kernel launches as recorded by the
+        library on the launching stream, number of those launches)."""
+        ctx.set_param(isw.PARAM_TIMING, 1)
+        ctx.timing(reset=True)
+        t = timed(fn)
+        k_ms, k_n, _ = ctx.timing(reset=True)
+        ctx.set_param(isw.PARAM_TIMING, 0)
+        return t, k_ms / max(k_n, 1)
+
     fp64 = None
     theta64 = None
     if not args.skip_fp64:
         theta64 = torch.empty_like(theta_d)
-        ms64 = timed(lambda: step(nodes_d, loops_d, theta64, prec="f64", fl=0))
-        fp64 = {"value": pairs_step / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64}
+        ms64, k64 = timed_kernel(lambda: step(nodes_d, loops_d, theta64, prec="f64", fl=0))
+        ach64 = FLOPS_PER_PAIR * pairs_step / (k64 / 1e3) / 1e12
+        fp64 = {"value": pairs_step / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": fma64, "unit": "TFLOP/s",
+                             "frac": ach64 / fma64, "frac_kind": "algorithmic (36 flop/pair) of measured",
+                             "traffic": None, "kernel": "isw::k_map_f64 (+ chunk reduce)",
+                             "kernel_ms": k64, "flops_per_pair": FLOPS_PER_PAIR,
+                             "peak_note": "measured: FP64 FMA-chain calibration kernel on every SM "
+                                          "(isw_fma_rate), this run"}}
 
     extra = {}
     if not args.skip_extra and rank == 0:
@@ -298,12 +335,28 @@ def run_gpu(args):
                           generator=torch.Generator(device=dev).manual_seed(args.seed + 1)) * th3.std()
         g3 = 2 * (th3 - tgt)
         gout = torch.empty((6, w3.n), dtype=torch.float64, device=dev)
-        isw.isw_map_adjoint(w3.nside, s3, g3, prec="f32c", out=gout)
-        ms3 = timed(lambda: isw.isw_map_adjoint(w3.nside, s3, g3, prec="f32c", out=gout))
-        ms3_64 = timed(lambda: isw.isw_map_adjoint(w3.nside, s3, g3, prec="f64", out=gout))
+        adj32 = lambda: isw.isw_map_adjoint(w3.nside, s3, g3, prec="f32c", out=gout)
+        adj64 = lambda: isw.isw_map_adjoint(w3.nside, s3, g3, prec="f64", out=gout)
+        adj32()
+        ms3, ka32 = timed_kernel(adj32)
+        ms3_64, ka64 = timed_kernel(adj64)
+        p3 = w3.npix * w3.n
+        peak32, _ = fp32_peak_tflops(sm_count)
+        a32 = ADJ_FLOPS_PER_PAIR * p3 / (ka32 / 1e3) / 1e12
+        a64 = ADJ_FLOPS_PER_PAIR * p3 / (ka64 / 1e3) / 1e12
         extra["adjoint"] = {"workload": f"{w3.name}: Nside={w3.nside}, {w3.n:,} samples, dL/dX and dL/dXdot",
-                            "value": w3.npix * w3.n / (ms3 / 1e3), "unit": UNIT, "ms": ms3,
-                            "fp64_value": w3.npix * w3.n / (ms3_64 / 1e3), "fp64_ms": ms3_64}
+                            "value": p3 / (ms3 / 1e3), "unit": UNIT, "ms": ms3,
+                            "fp64_value": p3 / (ms3_64 / 1e3), "fp64_ms": ms3_64,
+                            "roofline": {"bound": "alu", "achieved": a32, "peak": peak32, "unit": "TFLOP/s",
+                                         "frac": a32 / peak32, "flops_per_pair": ADJ_FLOPS_PER_PAIR,
+                                         "frac_kind": "algorithmic (66 flop/pair) of the derived FP32 peak",
+                                         "kernel": "isw::k_adj_f32c (+ chunk reduce)",
+                                         "kernel_ms": ka32, "traffic": None},
+                            "fp64_roofline": {"bound": "alu", "achieved": a64, "peak": fma64, "unit": "TFLOP/s",
+                                              "frac": a64 / fma64, "flops_per_pair": ADJ_FLOPS_PER_PAIR,
+                                              "frac_kind": "algorithmic (66 flop/pair) of the measured FP64 peak",
+                                              "kernel": "isw::k_adj_f64 (+ chunk reduce)",
+                                              "kernel_ms": ka64, "traffic": None}}
         # gradient through the light-cone solve: map adjoint with the dsigma row, then the
         # loop-parameter chain (98 Burden loops)
         tau3 = torch.empty(w3.n, dtype=torch.float64, device=dev)
@@ -381,14 +434,18 @@ def run_gpu(args):
         if r != isw.OK:
             raise RuntimeError(f"device status {r} in the extra measurements: {ctx.last_error()}")
 
-    peak, mhz = fp32_peak_tflops()
+    peak, mhz = fp32_peak_tflops(sm_count)
     map_avg_ms = map_ms / max(map_launches, 1)
     achieved = FLOPS_PER_PAIR * pairs_step / (map_avg_ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "frac_kind": "algorithmic: 36 textbook flops per pair (the far-field form executes ~15 FP32 "
+                         "lane operations per pair) of the derived FP32 peak",
+            "fma_pipe_busy_far_pass": (profiled_fma_busy(variant_used) if args.nside is None else None),
             "traffic": (profiled_traffic(variant_used) if args.nside is None else None),
             "kernel": f"pair kernels: isw::k_map_f32c (far field) + k_map_f32c_near + chunk reduce, variant {variant_used}",
             "flops_per_pair": FLOPS_PER_PAIR, "kernel_ms": map_avg_ms, "kernel_launches": map_launches,
-            "peak_note": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz (max SM clock)"}
+            "peak_note": f"derived: {sm_count} SMs (device) x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz "
+                         f"(max SM clock); measured FP32 FMA calibration kernel: {fma32:.1f} TFLOP/s"}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -398,6 +455,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": int(theta_h.numel() * 8), "ms_per_step": e2e_ms},
         "gpu_launches": int(all_launches),
         "fp64": fp64, "speedup_fp32c_vs_fp64": (value / ws) / fp64["value"] if fp64 else None,
+        "measured_fma_peaks": {"fp32_tflops": fma32, "fp64_tflops": fma64, "sm_count": sm_count},
         "counts_per_step": {k: v / args.steps for k, v in counts.items()},
         "wall_s_timed_region": t_wall,
     }
@@ -484,6 +542,53 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_case(args):
+    """One small, self-contained invocation of a single pair kernel, for profiling with ncu (it
+    prints one line of timing, not the bench line):
+      map_f64       the plain FP64 map of synth.config(0): Nside 64, 10,240 Burden-loop samples
+      adjoint_f32c  the FP32-compensated adjoint of synth.config(3) (50,176 samples) at Nside 128
+      adjoint_f64   the FP64 adjoint of the same
+      map_f32c      the FP32-compensated map of synth.config(1) (200,000 samples) at Nside 128
+    Each runs --warmup untimed calls and then --steps timed ones."""
+    import torch
+
+    import paper_1204_5041_gb300 as isw
+
+    dev = torch.device("cuda", 0)
+    cfg = {"map_f64": 0, "adjoint_f32c": 3, "adjoint_f64": 3, "map_f32c": 1}[args.case]
+    w = synth.config(cfg, seed=args.seed)
+    nside = args.nside or {0: 64, 3: 128, 1: 128}[cfg]
+    nodes = torch.from_numpy(np.ascontiguousarray(w.nodes)).to(dev)
+    loops = torch.from_numpy(np.ascontiguousarray(w.loop_params)).to(dev)
+    samples = isw.lightcone_intersect_shells(nodes, w.shell_off, w.t_box, w.mode, loops, x_obs=w.x_obs,
+                                             t_obs=w.t_obs)
+    npix = 12 * nside * nside
+    if args.case.startswith("map"):
+        prec = args.case[4:]
+        out = torch.empty(npix, dtype=torch.float64, device=dev)
+        fn = lambda: isw.isw_map(nside, samples, x_obs=w.x_obs, GU=w.GU, prec=prec, out=out)
+    else:
+        prec = args.case[8:]
+        g = torch.randn(npix, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+        out = torch.empty((6, w.n), dtype=torch.float64, device=dev)
+        fn = lambda: isw.isw_map_adjoint(nside, samples, g, x_obs=w.x_obs, GU=w.GU, prec=prec, out=out)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    r, _ = isw.default_context(0).check_status()
+    if r != isw.OK:
+        raise RuntimeError(f"device status {r}")
+    print(f"case {args.case}: Nside={nside} ({npix} pixels) x {w.n} samples = {npix * w.n:.3e} pairs, "
+          f"{ms:.3f} ms per call, {npix * w.n / (ms / 1e3):.3e} pairs/s")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,10 +608,14 @@ def main():
     ap.add_argument("--near-k", type=float, default=None, help="near-field radius factor (default 4)")
     ap.add_argument("--nside", type=int, default=None,
                     help="override the sky resolution (smaller skies for profiling; the bench line uses 512)")
+    ap.add_argument("--case", choices=["map_f64", "map_f32c", "adjoint_f32c", "adjoint_f64"], default=None,
+                    help="run one small pair-kernel case for profiling instead of the benchmark")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl != "reference":
+    if args.warmup < 3 and args.impl != "reference" and args.case is None:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.case is not None:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -16,7 +16,9 @@
  * Planck units; maps scale linearly with it.
  *
  * Memory: every array argument is a DEVICE pointer owned by the caller (for example a
- * PyTorch CUDA tensor's data pointer), except where marked (host).  Arrays of several rows
+ * PyTorch CUDA tensor's data pointer), except where marked (host).  Device arrays must live on
+ * the context's GPU (or be managed memory); a pointer to host memory or to another GPU's memory
+ * is rejected with ISW_EINVAL before anything is enqueued.  Arrays of several rows
  * are row-major "double[rows][ld]": element (r, k) sits at base[r * ld + k].  The library
  * allocates only its own workspace, held in the context and freed by isw_destroy.
  *
@@ -70,7 +72,8 @@ enum {
     ISW_PARAM_VARIANT = 3,
     ISW_PARAM_TIMING = 4,
     ISW_PARAM_D_FAR = 5,
-    ISW_PARAM_NUM_VARIANTS = 6   /* read-only (isw_get_param): number of FP32 kernel variants */
+    ISW_PARAM_NUM_VARIANTS = 6,  /* read-only (isw_get_param): number of FP32 kernel variants */
+    ISW_PARAM_WAIT_POLLS = 7
 };
 
 /* Create a context bound to CUDA device `device`.  Allocates a small device status block.
@@ -101,7 +104,13 @@ int isw_check_status(isw_ctx *ctx, void *stream, int64_t *counts);
  * when 1, every launch of the pair kernel (the all-pairs sum of isw_map and
  * isw_map_batched: the FP32 far- and near-field passes and the chunk reduction between them, or
  * the FP64 kernel and its reduction) is bracketed by CUDA events on its stream, read by
- * isw_get_timing. */
+ * isw_get_timing.  ISW_PARAM_WAIT_POLLS (default 2^22; a negative value restores it): the
+ * limit, in mbarrier try_wait polls, of every wait of the pair kernels (isw_map, isw_map_batched,
+ * isw_map_adjoint, isw_map_patch) for a stage of records to land in shared memory.  A wait that
+ * runs out stops its block: the block waits for its own copies still in flight (a separate limit
+ * of 2^26 polls), records ISW_ETIMEOUT and returns, so the output is incomplete and
+ * isw_check_status returns ISW_ETIMEOUT.  0 makes every wait give up at once, which exercises
+ * this failure path without a fault. */
 int isw_set_param(isw_ctx *ctx, int key, double value);
 
 /* Read a tunable into *value (host pointer).  For ISW_PARAM_VARIANT the value is the FP32
@@ -116,6 +125,13 @@ int isw_get_param(const isw_ctx *ctx, int key, double *value);
  * three are host pointers and may be NULL.  reset = 1 clears the record.  At most 4096
  * pair-kernel launches are timed between resets (later ones are counted, not timed). */
 int isw_get_timing(isw_ctx *ctx, double *ms, int64_t *pair_launches, int64_t *all_launches, int reset);
+
+/* Measured throughput of the GPU's fused multiply-add pipe, the peak against which the pair
+ * kernels' FP32 (prec = ISW_F32C) or FP64 (prec = ISW_F64) arithmetic is stated (the paper has no
+ * counterpart: it times CPU cores).  A calibration kernel runs independent FMA chains on every
+ * SM; *flop_per_s (host) receives the best of three timed launches, an FMA counting two flops.
+ * Synchronises `stream`; takes a few milliseconds (FP32) to tens of milliseconds (FP64). */
+int isw_fma_rate(isw_ctx *ctx, int prec, double *flop_per_s, void *stream);
 
 /* Pixel centres, HEALPix RING scheme (Sec. II.D; Gorski et al. 2005 geometry).
  *   nside    : resolution N >= 1 (N_pix = 12 N^2), N <= 2^24
@@ -310,12 +326,17 @@ int isw_map_batched(isw_ctx *ctx, int64_t nside, const double *nodes, int64_t ld
  *   - All calls share the array and it keeps the last call's contents; each call clears
  *     what must start at zero.  Calls that overlap on the GPU (for example on two streams
  *     without ordering) race on the array and produce wrong maps.
- *   - Arguments as in isw_map (device samples double[10][ld], device theta_out double[npix],
- *     host x_obs or NULL); near-field and b_min settings are the defaults of isw_map.
- *     Device-side conditions (skipped samples) are not reported; use isw_map with
- *     isw_check_status to diagnose an input. */
+ *   - Arguments as in isw_map (device samples double[10][ld] and theta_out double[npix] on the
+ *     current device, host x_obs or NULL); kernel variant, segment chunks, near-field and b_min
+ *     settings are those of isw_map with default settings (the chunk count capped by the
+ *     scratch), so the map equals isw_map's.
+ *   - status_out (host, may be NULL): when given, the call waits for `stream` and stores the
+ *     status the kernels recorded: ISW_OK, ISW_EDOMAIN (a sample with |Xdot| >= 1 or a
+ *     non-finite weight was skipped) or ISW_ETIMEOUT (a bounded device wait ran out: the map is
+ *     incomplete).  Without it the call does not synchronise and such conditions go unreported.
+ *     The return value is the host-side status (argument checks and launches). */
 int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, const double *samples, int64_t n, int64_t ld,
-                         const double *x_obs, double GU, double *theta_out, void *stream);
+                         const double *x_obs, double GU, double *theta_out, int32_t *status_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -94,6 +94,10 @@ def lib():
             L.or_isw_map_patch.restype = ctypes.c_int
             L.or_map_alm_cl.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, _dp, _dp]
             L.or_map_alm_cl.restype = ctypes.c_int
+            L.or_map_alm_m.argtypes = [ctypes.c_int64, _dp, ctypes.c_int64, ctypes.c_int64, _dp, _dp]
+            L.or_map_alm_m.restype = ctypes.c_int
+            L.or_cl_from_alm.argtypes = [ctypes.c_int64, _dp, _dp]
+            L.or_cl_from_alm.restype = None
             L.or_ring_info.argtypes = [ctypes.c_int64, ctypes.c_int64, _dp, _i64p, _i64p, _dp]
             L.or_ring_info.restype = None
             L.or_legendre_column.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int64, _dp]
@@ -390,18 +394,61 @@ def isw_map_patch(frame, M: int, width: float, samples, approx: int = FULLSKY, x
     return theta.reshape(M, M)
 
 
-def map_alm_cl(nside: int, theta, lmax: int):
+def map_alm_cl(nside: int, theta, lmax: int, threads: int = 1):
     """Spherical-harmonic analysis of a full-sky RING map: returns (alm complex [mmax+1, lmax+1],
-    only l >= m filled; cl [lmax+1])."""
+    only l >= m filled; cl [lmax+1]).  With threads > 1 the values of m are split across threads
+    (each m is an independent single-threaded call; the result is the same)."""
     theta = _c64(theta)
     assert theta.size == 12 * nside * nside
     alm = np.zeros(2 * (lmax + 1) * (lmax + 1))
     cl = np.zeros(lmax + 1)
-    r = lib().or_map_alm_cl(int(nside), _d(theta), int(lmax), _d(alm), _d(cl))
-    if r:
-        raise ValueError(f"or_map_alm_cl failed with status {r}")
+    if threads <= 1:
+        r = lib().or_map_alm_cl(int(nside), _d(theta), int(lmax), _d(alm), _d(cl))
+        if r:
+            raise ValueError(f"or_map_alm_cl failed with status {r}")
+    else:
+        a = alm.reshape(2, lmax + 1, lmax + 1)
+        a[...] = map_alm_m(nside, theta, lmax, np.arange(lmax + 1), threads=threads)
+        lib().or_cl_from_alm(int(lmax), _d(alm), _d(cl))
     a = alm.reshape(2, lmax + 1, lmax + 1)
     return a[0] + 1j * a[1], cl
+
+
+def map_alm_m(nside: int, theta, lmax: int, ms, threads: int = 1):
+    """a_lm of a full-sky RING map for the listed m only: float64 [2 (re, im), len(ms), lmax+1]."""
+    theta = _c64(theta)
+    assert theta.size == 12 * nside * nside
+    ms = [int(m) for m in ms]
+    out = np.zeros((2, len(ms), lmax + 1))
+    L = lib()
+    errors = []
+    nxt = [0]
+    lk = threading.Lock()
+
+    def work():
+        re = np.empty(lmax + 1)
+        im = np.empty(lmax + 1)
+        while True:
+            with lk:
+                k = nxt[0]
+                nxt[0] += 1
+            if k >= len(ms):
+                return
+            r = L.or_map_alm_m(int(nside), _d(theta), int(lmax), ms[k], _d(re), _d(im))
+            if r:
+                errors.append(r)
+                return
+            out[0, k] = re
+            out[1, k] = im
+
+    ths = [threading.Thread(target=work) for _ in range(max(1, min(threads, len(ms))))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    if errors:
+        raise ValueError(f"or_map_alm_m failed with status {errors[0]}")
+    return out
 
 
 def ring_info(nside: int, i: int):

@@ -1164,52 +1164,47 @@ void or_ring_info(int64_t N, int64_t i, double *z, int64_t *np, int64_t *p0, dou
     ring_info(N, i, z, np, p0, t0);
 }
 
-/* alm: double[2][mmax+1][lmax+1] (re then im), only l >= m filled; cl: double[lmax+1] */
-int or_map_alm_cl(int64_t N, const double *map, int64_t lmax, double *alm, double *cl)
+/* a_lm of one m, l = 0 .. lmax, into re[l], im[l] (zero for l < m): the Fourier sum of every
+ * ring at this m (Neumaier, exact phase reduction), then the Legendre sum over the rings in
+ * ring order.  Independent m give independent coefficients, so callers may split m freely. */
+int or_map_alm_m(int64_t N, const double *map, int64_t lmax, int64_t m, double *re, double *im)
 {
-    if (N < 1 || lmax < 0) return OR_EINVAL;
-    int64_t mmax = lmax, nring = 4 * N - 1, npix = 12 * N * N;
-    size_t L1 = (size_t)(lmax + 1), M1 = (size_t)(mmax + 1);
-    double *Fre = (double *)calloc((size_t)nring * M1, sizeof(double));
-    double *Fim = (double *)calloc((size_t)nring * M1, sizeof(double));
-    double *zr = (double *)malloc((size_t)nring * sizeof(double));
+    if (N < 1 || lmax < 0 || m < 0 || m > lmax) return OR_EINVAL;
+    int64_t nring = 4 * N - 1, npix = 12 * N * N;
+    size_t L1 = (size_t)(lmax + 1);
     double *lam = (double *)malloc(L1 * sizeof(double));
-    if (!Fre || !Fim || !zr || !lam) {
-        free(Fre); free(Fim); free(zr); free(lam);
-        return OR_EINVAL;
-    }
+    if (!lam) return OR_EINVAL;
+    for (size_t l = 0; l < L1; ++l) re[l] = im[l] = 0.0;
+    const double omega = 4.0 * PI / (double)npix;
     for (int64_t r = 0; r < nring; ++r) {
         double z, t0;
         int64_t np, p0;
         ring_info(N, r + 1, &z, &np, &p0, &t0);
-        zr[r] = z;
-        for (int64_t m = 0; m <= mmax; ++m) {
-            double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
-            for (int64_t j = 0; j < np; ++j) {
-                /* m phi / (2 pi) = m (t0 + j/np), reduced exactly: (m j mod np) / np + m t0 */
-                double w = (double)((m * j) % np) / (double)np + (double)m * t0;
-                double s, c;
-                or_sincos_turns(w, &s, &c);
-                double v = map[p0 + j];
-                neumaier(&sr, &cr, v * c);
-                neumaier(&si, &ci, -(v * s));
-            }
-            Fre[(size_t)r * M1 + m] = sr + cr;
-            Fim[(size_t)r * M1 + m] = si + ci;
+        double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+        for (int64_t j = 0; j < np; ++j) {
+            /* m phi / (2 pi) = m (t0 + j/np), reduced exactly: (m j mod np) / np + m t0 */
+            double w = (double)((m * j) % np) / (double)np + (double)m * t0;
+            double s, c;
+            or_sincos_turns(w, &s, &c);
+            double v = map[p0 + j];
+            neumaier(&sr, &cr, v * c);
+            neumaier(&si, &ci, -(v * s));
+        }
+        const double Fre = sr + cr, Fim = si + ci;
+        legendre_column(z, m, lmax, lam);
+        for (int64_t l = m; l <= lmax; ++l) {
+            re[l] += omega * (lam[l] * Fre);
+            im[l] += omega * (lam[l] * Fim);
         }
     }
-    const double omega = 4.0 * PI / (double)npix;
-    for (size_t q = 0; q < 2 * M1 * L1; ++q) alm[q] = 0.0;
-    for (int64_t m = 0; m <= mmax; ++m) {
-        for (int64_t r = 0; r < nring; ++r) {
-            legendre_column(zr[r], m, lmax, lam);
-            for (int64_t l = m; l <= lmax; ++l) {
-                size_t q = (size_t)m * L1 + (size_t)l;
-                alm[q] += omega * (lam[l] * Fre[(size_t)r * M1 + m]);
-                alm[M1 * L1 + q] += omega * (lam[l] * Fim[(size_t)r * M1 + m]);
-            }
-        }
-    }
+    free(lam);
+    return OR_OK;
+}
+
+/* C_l = (|a_l0|^2 + 2 sum_{m>=1} |a_lm|^2) / (2l + 1) from alm: double[2][lmax+1][lmax+1] */
+void or_cl_from_alm(int64_t lmax, const double *alm, double *cl)
+{
+    size_t L1 = (size_t)(lmax + 1), M1 = L1;
     for (int64_t l = 0; l <= lmax; ++l) {
         double s = 0.0;
         for (int64_t m = 0; m <= l; ++m) {
@@ -1219,6 +1214,17 @@ int or_map_alm_cl(int64_t N, const double *map, int64_t lmax, double *alm, doubl
         }
         cl[l] = s / (2.0 * l + 1.0);
     }
-    free(Fre); free(Fim); free(zr); free(lam);
+}
+
+/* alm: double[2][mmax+1][lmax+1] (re then im), only l >= m filled; cl: double[lmax+1] */
+int or_map_alm_cl(int64_t N, const double *map, int64_t lmax, double *alm, double *cl)
+{
+    if (N < 1 || lmax < 0) return OR_EINVAL;
+    size_t L1 = (size_t)(lmax + 1), M1 = L1;
+    for (int64_t m = 0; m <= lmax; ++m) {
+        int r = or_map_alm_m(N, map, lmax, m, alm + (size_t)m * L1, alm + M1 * L1 + (size_t)m * L1);
+        if (r) return r;
+    }
+    or_cl_from_alm(lmax, alm, cl);
     return OR_OK;
 }

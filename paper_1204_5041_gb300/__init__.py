@@ -30,7 +30,8 @@ F64, F32C = 0, 1
 LINEAR, BURDEN = 0, 1
 FULLSKY, FLATSKY = 0, 1
 SKIP_LIGHTCONE, GRAPH, AUTOTUNE = 1, 2, 4
-PARAM_NEAR_K, PARAM_B_MIN, PARAM_SPLIT, PARAM_VARIANT, PARAM_TIMING, PARAM_D_FAR, PARAM_NUM_VARIANTS = range(7)
+(PARAM_NEAR_K, PARAM_B_MIN, PARAM_SPLIT, PARAM_VARIANT, PARAM_TIMING, PARAM_D_FAR, PARAM_NUM_VARIANTS,
+ PARAM_WAIT_POLLS) = range(8)
 _STATUS_NAMES = {0: "ISW_OK", 1: "ISW_EINVAL", 2: "ISW_ECUDA", 3: "ISW_EDOMAIN", 4: "ISW_ENOCONV",
                  5: "ISW_ETIMEOUT", 6: "ISW_ENOMEM"}
 
@@ -64,6 +65,7 @@ def lib():
                 "isw_destroy": (_i32, [_vp]),
                 "isw_last_error": (ctypes.c_char_p, [_vp]),
                 "isw_check_status": (_i32, [_vp, _vp, ctypes.POINTER(_i64)]),
+                "isw_fma_rate": (_i32, [_vp, _i32, ctypes.POINTER(_dbl), _vp]),
                 "isw_set_param": (_i32, [_vp, _i32, _dbl]),
                 "isw_get_param": (_i32, [_vp, _i32, ctypes.POINTER(_dbl)]),
                 "isw_get_timing": (_i32, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
@@ -146,10 +148,16 @@ class Context:
         self.check(lib().isw_get_timing(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(m), int(reset)))
         return ms.value, n.value, m.value
 
+    def fma_rate(self, prec="f32c", stream=None) -> float:
+        """Measured FMA-pipe throughput of this context's GPU in flop/s (FMA = 2 flops), FP32 or FP64."""
+        v = _dbl()
+        self.check(lib().isw_fma_rate(self._h, _precision(prec), ctypes.byref(v), _stream(stream, self.device)))
+        return v.value
+
     def check_status(self, stream=None, raise_on_error: bool = False):
         """Synchronise the stream; return (status code, counts dict) and clear the device status."""
         counts = (_i64 * 3)()
-        r = lib().isw_check_status(self._h, _stream(stream), counts)
+        r = lib().isw_check_status(self._h, _stream(stream, self.device), counts)
         if raise_on_error and r != OK:
             raise ISWError(r, self.last_error())
         return r, {"zero_pairs": counts[0], "skipped_samples": counts[1], "near_pairs": counts[2]}
@@ -166,9 +174,10 @@ def default_context(device: int | None = None) -> Context:
     return _contexts[device]
 
 
-def _stream(stream):
+def _stream(stream, device=None):
+    """The stream handle: the given one, else torch's current stream of ``device``."""
     if stream is None:
-        return _vp(torch.cuda.current_stream().cuda_stream)
+        return _vp(torch.cuda.current_stream(device).cuda_stream)
     if isinstance(stream, torch.cuda.Stream):
         return _vp(stream.cuda_stream)
     return _vp(int(stream))
@@ -187,14 +196,18 @@ def _dev_tensor(t, dtype, name):
 
 
 def _rows(t, nrows, name):
-    """A [nrows, n] tensor with unit stride along n -> (tensor, n, ld)."""
+    """A [nrows, n] tensor with unit stride along n and rows that do not overlap -> (n, ld)."""
     if t.dim() != 2 or t.shape[0] != nrows:
         raise ValueError(f"{name} must have shape [{nrows}, n]")
-    if t.shape[1] > 0 and t.stride(1) != 1:
-        raise ValueError(f"{name} must have unit stride along its last axis")
     n = t.shape[1]
-    ld = t.stride(0) if nrows > 1 else max(n, 1)
-    return n, max(ld, n)
+    if n > 0 and t.stride(1) != 1:
+        raise ValueError(f"{name} must have unit stride along its last axis")
+    if nrows == 1 or n == 0:
+        return n, max(n, 1)
+    if t.stride(0) < n:
+        # rows that overlap (an expand() has stride 0): the library would read past the storage
+        raise ValueError(f"{name} has row stride {t.stride(0)} < {n}: rows must not overlap")
+    return n, t.stride(0)
 
 
 def _xobs(x_obs):
@@ -202,8 +215,14 @@ def _xobs(x_obs):
     return (_dbl * 3)(*x)
 
 
-def _ctx(ctx):
-    return ctx if ctx is not None else default_context()
+def _ctx(ctx, t=None):
+    """The given context, else the default context of the GPU that holds tensor ``t`` (the
+    current device when no tensor is given): the kernels must run where the data lives."""
+    if ctx is not None:
+        return ctx
+    if t is not None and getattr(t, "is_cuda", False):
+        return default_context(t.device.index if t.device.index is not None else torch.cuda.current_device())
+    return default_context()
 
 
 def _precision(prec) -> int:
@@ -226,20 +245,21 @@ def _pixels(nside, pix, pix0, npix):
 def hp_pix2vec_ring(nside: int, pix=None, pix0: int = 0, npix: int | None = None, out=None, ctx=None,
                     stream=None, device=None):
     """RING pixel centres as a float64 CUDA tensor [3, npix]."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, out if out is not None else pix)
     pix, pix0, npix = _pixels(nside, pix, pix0, npix)
     if out is None:
         out = torch.empty((3, npix), dtype=torch.float64, device=device or f"cuda:{c.device}")
     _dev_tensor(out, torch.float64, "out")
     n, ld = _rows(out, 3, "out")
-    c.check(lib().hp_pix2vec_ring(c.handle, int(nside), pix0, npix, _ptr(pix), _ptr(out), ld, _stream(stream)))
+    c.check(lib().hp_pix2vec_ring(c.handle, int(nside), pix0, npix, _ptr(pix), _ptr(out), ld,
+                                  _stream(stream, c.device)))
     return out
 
 
 def lightcone_intersect(mode: int, nodes, loop_params=None, t_box: float = 0.0, x_obs=None, t_obs: float = 1.0,
                         out=None, tau=None, status=None, ctx=None, stream=None):
     """Samples on the observer's past light cone: float64 CUDA tensor [10, n] (and tau, status if given)."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, nodes)
     _dev_tensor(nodes, torch.float64, "nodes")
     n, ld = _rows(nodes, 10, "nodes")
     if out is None:
@@ -258,14 +278,14 @@ def lightcone_intersect(mode: int, nodes, loop_params=None, t_box: float = 0.0, 
         _dev_tensor(status, torch.int32, "status")
     c.check(lib().lightcone_intersect(c.handle, int(mode), _ptr(nodes), n, ld, _ptr(P), nloops, ldp, float(t_box),
                                       _xobs(x_obs), float(t_obs), _ptr(out), ld_out, _ptr(tau), _ptr(status),
-                                      _stream(stream)))
+                                      _stream(stream, c.device)))
     return out
 
 
 def isw_map(nside: int, samples, pix=None, pix0: int = 0, npix: int | None = None, x_obs=None, GU: float = 1.0,
             prec="f32c", accumulate: bool = False, out=None, ctx=None, stream=None):
     """Theta of Eq. (1)-(2) at the selected pixels: float64 CUDA tensor [npix]."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, samples)
     _dev_tensor(samples, torch.float64, "samples")
     n, ld = _rows(samples, 10, "samples")
     pix, pix0, npix = _pixels(nside, pix, pix0, npix)
@@ -275,7 +295,8 @@ def isw_map(nside: int, samples, pix=None, pix0: int = 0, npix: int | None = Non
     if out.numel() != npix or not out.is_contiguous():
         raise ValueError("out must be a contiguous float64 tensor of npix elements")
     c.check(lib().isw_map(c.handle, int(nside), pix0, npix, _ptr(pix), _ptr(samples), n, ld, _xobs(x_obs),
-                          float(GU), _precision(prec), int(bool(accumulate)), _ptr(out), _stream(stream)))
+                          float(GU), _precision(prec), int(bool(accumulate)), _ptr(out),
+                          _stream(stream, c.device)))
     return out
 
 
@@ -283,7 +304,7 @@ def isw_map_adjoint(nside: int, samples, dL_dtheta, pix=None, pix0: int = 0, npi
                     GU: float = 1.0, prec="f32c", ngrad: int = 6, out=None, ctx=None, stream=None):
     """dL/dX, dL/dXdot (then dL/dX' when ngrad >= 9 and dL/ddsigma when ngrad = 10) per sample:
     float64 CUDA tensor [ngrad, n]."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, samples)
     _dev_tensor(samples, torch.float64, "samples")
     n, ld = _rows(samples, 10, "samples")
     pix, pix0, npix = _pixels(nside, pix, pix0, npix)
@@ -299,7 +320,7 @@ def isw_map_adjoint(nside: int, samples, dL_dtheta, pix=None, pix0: int = 0, npi
     _, ld_g = _rows(out, ngrad, "out")
     c.check(lib().isw_map_adjoint(c.handle, int(nside), pix0, npix, _ptr(pix), _ptr(samples), n, ld, _xobs(x_obs),
                                   float(GU), _precision(prec), _ptr(g), _ptr(out), ld_g, int(ngrad),
-                                  _stream(stream)))
+                                  _stream(stream, c.device)))
     return out
 
 
@@ -309,7 +330,7 @@ def isw_map_batched(nside: int, nodes, shell_off, t_box, mode, loop_params=None,
     """One full-sky RING map summed over many shells (host shell metadata, device nodes)."""
     import numpy as np
 
-    c = _ctx(ctx)
+    c = _ctx(ctx, nodes)
     _dev_tensor(nodes, torch.float64, "nodes")
     n, ld = _rows(nodes, 10, "nodes")
     off = np.ascontiguousarray(np.asarray(shell_off, dtype=np.int64))
@@ -330,7 +351,7 @@ def isw_map_batched(nside: int, nodes, shell_off, t_box, mode, loop_params=None,
     c.check(lib().isw_map_batched(c.handle, int(nside), _ptr(nodes), ld, off.ctypes.data_as(_vp), nshell,
                                   tb.ctypes.data_as(_vp), md.ctypes.data_as(_vp), _ptr(P), nloops, ldp, _xobs(x_obs),
                                   float(t_obs), float(GU), _precision(prec), int(flags), int(bool(accumulate)),
-                                  _ptr(out), _stream(stream)))
+                                  _ptr(out), _stream(stream, c.device)))
     return out
 
 
@@ -340,7 +361,7 @@ def lightcone_adjoint(mode: int, nodes, tau, grad_samples, loop_params=None, t_b
     light-cone solve.  Returns (grad_nodes [10, n], grad_loops [17, nloops] or None for LINEAR):
     LINEAR gives the box-time node gradients; BURDEN gives node rows 1 (sigma) and 9 (dsigma) and
     the per-loop parameter gradients (the nodes of one loop must be contiguous)."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, nodes)
     _dev_tensor(nodes, torch.float64, "nodes")
     n, ld = _rows(nodes, 10, "nodes")
     _dev_tensor(tau, torch.float64, "tau")
@@ -372,7 +393,7 @@ def lightcone_adjoint(mode: int, nodes, tau, grad_samples, loop_params=None, t_b
         out_loops = None
     c.check(lib().lightcone_adjoint(c.handle, int(mode), _ptr(nodes), n, ld, _ptr(P), nloops, ldp, float(t_box),
                                     _xobs(x_obs), _ptr(tau), _ptr(grad_samples), ld_gs, int(ngrad), _ptr(out), ld_gn,
-                                    _ptr(out_loops), ld_gl, _stream(stream)))
+                                    _ptr(out_loops), ld_gl, _stream(stream, c.device)))
     return out, out_loops
 
 
@@ -428,13 +449,14 @@ class ISWLightconeMap(torch.autograd.Function):
 
 def hp_vec2pix_ring(nside: int, vec, out=None, ctx=None, stream=None):
     """RING pixel of each direction (columns of a float64 CUDA tensor [3, n]): int64 tensor [n]."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, vec)
     _dev_tensor(vec, torch.float64, "vec")
     n, ld = _rows(vec, 3, "vec")
     if out is None:
         out = torch.empty(n, dtype=torch.int64, device=vec.device)
     _dev_tensor(out, torch.int64, "out")
-    c.check(lib().hp_vec2pix_ring(c.handle, int(nside), _ptr(vec), n, ld, _ptr(out), _stream(stream)))
+    c.check(lib().hp_vec2pix_ring(c.handle, int(nside), _ptr(vec), n, ld, _ptr(out),
+                                  _stream(stream, c.device)))
     return out
 
 
@@ -449,7 +471,7 @@ def lightcone_intersect_shells(nodes, shell_off, t_box, mode, loop_params=None, 
     """Light-cone samples of many shells in one launch: float64 CUDA tensor [10, n]."""
     import numpy as np
 
-    c = _ctx(ctx)
+    c = _ctx(ctx, nodes)
     _dev_tensor(nodes, torch.float64, "nodes")
     n, ld = _rows(nodes, 10, "nodes")
     off = _host_i64(shell_off)
@@ -467,7 +489,8 @@ def lightcone_intersect_shells(nodes, shell_off, t_box, mode, loop_params=None, 
     _, ld_out = _rows(out, 10, "out")
     c.check(lib().lightcone_intersect_shells(c.handle, _ptr(nodes), ld, off.ctypes.data_as(_vp), tb.size,
                                              tb.ctypes.data_as(_vp), md.ctypes.data_as(_vp), _ptr(P), nloops, ldp,
-                                             _xobs(x_obs), float(t_obs), _ptr(out), ld_out, _stream(stream)))
+                                             _xobs(x_obs), float(t_obs), _ptr(out), ld_out,
+                                             _stream(stream, c.device)))
     return out
 
 
@@ -476,7 +499,7 @@ def box_place(nodes_box, box_off, shell_box, place, out=None, ctx=None, stream=N
     shell_off_out host int64 array)."""
     import numpy as np
 
-    c = _ctx(ctx)
+    c = _ctx(ctx, nodes_box)
     _dev_tensor(nodes_box, torch.float64, "nodes_box")
     _, ldb = _rows(nodes_box, 10, "nodes_box")
     boff, sbox = _host_i64(box_off), _host_i64(shell_box)
@@ -490,7 +513,7 @@ def box_place(nodes_box, box_off, shell_box, place, out=None, ctx=None, stream=N
     off = np.zeros(sbox.size + 1, dtype=np.int64)
     c.check(lib().box_place(c.handle, _ptr(nodes_box), ldb, boff.ctypes.data_as(_vp), boff.size - 1,
                             sbox.ctypes.data_as(_vp), sbox.size, _ptr(place), _ptr(out), ld_out,
-                            off.ctypes.data_as(_vp), _stream(stream)))
+                            off.ctypes.data_as(_vp), _stream(stream, c.device)))
     return out[:, :n_out], off
 
 
@@ -498,7 +521,7 @@ def cone_cut(samples, shell_off, nside_hz: int, cone_pix, r_lo, r_hi, x_obs=None
     """Samples inside each shell's HEALPix cone and radius range, compacted in input order:
     returns (kept [10, m] CUDA tensor view, shell offsets int64 CUDA tensor [nshell + 1]).
     Synchronises the stream to read m."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, samples)
     _dev_tensor(samples, torch.float64, "samples")
     n, ld = _rows(samples, 10, "samples")
     off = _host_i64(shell_off)
@@ -517,7 +540,7 @@ def cone_cut(samples, shell_off, nside_hz: int, cone_pix, r_lo, r_hi, x_obs=None
     cnt = _i64(0)
     c.check(lib().cone_cut(c.handle, _ptr(samples), ld, off.ctypes.data_as(_vp), nshell, int(nside_hz),
                            _ptr(cone_pix), _ptr(r_lo), _ptr(r_hi), _xobs(x_obs), _ptr(out), ld_out, _ptr(off_out),
-                           ctypes.byref(cnt), _stream(stream)))
+                           ctypes.byref(cnt), _stream(stream, c.device)))
     return out[:, :cnt.value], off_out
 
 
@@ -541,7 +564,7 @@ def isw_map_patch(frame, M: int, width: float, samples, approx: int = FULLSKY, x
     coordinate width ``width``), full sky or flat sky: float64 CUDA tensor [M, M] (row j = eta)."""
     import numpy as np
 
-    c = _ctx(ctx)
+    c = _ctx(ctx, samples)
     fr = np.ascontiguousarray(np.asarray(frame, dtype=np.float64).reshape(9))
     _dev_tensor(samples, torch.float64, "samples")
     n, ld = _rows(samples, 10, "samples")
@@ -552,20 +575,21 @@ def isw_map_patch(frame, M: int, width: float, samples, approx: int = FULLSKY, x
         raise ValueError("out must be a contiguous float64 tensor of M*M elements")
     c.check(lib().isw_map_patch(c.handle, fr.ctypes.data_as(_vp), int(M), float(width), _ptr(samples), n, ld,
                                 _xobs(x_obs), float(GU), _precision(prec), int(approx), int(bool(accumulate)),
-                                _ptr(out), _stream(stream)))
+                                _ptr(out), _stream(stream, c.device)))
     return out
 
 
 def isw_map_cl(nside: int, theta, lmax: int, with_alm: bool = False, ctx=None, stream=None):
     """Angular power spectrum of a full-sky RING map (float64 CUDA tensor [12 nside^2]): returns
     cl [lmax + 1], or (alm complex [lmax + 1 (m), lmax + 1 (l)], cl) with ``with_alm``."""
-    c = _ctx(ctx)
+    c = _ctx(ctx, theta)
     _dev_tensor(theta, torch.float64, "theta")
     if theta.numel() != 12 * nside * nside or not theta.is_contiguous():
         raise ValueError("theta must be a contiguous full-sky RING map")
     cl = torch.empty(lmax + 1, dtype=torch.float64, device=theta.device)
     alm = torch.empty((2, lmax + 1, lmax + 1), dtype=torch.float64, device=theta.device) if with_alm else None
-    c.check(lib().isw_map_cl(c.handle, int(nside), _ptr(theta), int(lmax), _ptr(alm), _ptr(cl), _stream(stream)))
+    c.check(lib().isw_map_cl(c.handle, int(nside), _ptr(theta), int(lmax), _ptr(alm), _ptr(cl),
+                             _stream(stream, c.device)))
     if with_alm:
         return torch.complex(alm[0], alm[1]), cl
     return cl

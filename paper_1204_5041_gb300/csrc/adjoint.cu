@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
         for (; i < nt; ++i) {
             const uint32_t gi = gl + i;
             const int buf = gi % kStages;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else {
                 const int64_t pt = p0 + i;
@@ -271,10 +271,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
             if (tid == 0 && i + kStages < nt) issue_tile<Pix32, TP>(sbuf, bars, a.p32, p0 + i + kStages, gi + kStages);
         }
         if (s_abort) {
-            if (tid == 0) {
-                atomicOr(&a.st->bits, kStatTimeout);
-                drain<TP>(bars, gl, i, nt);
-            }
+            if (tid == 0) drain(bars, gl, i, i + kStages < nt ? i + kStages : nt, a.st);
             return;
         }
         gl += nt;
@@ -338,7 +335,7 @@ __global__ void __launch_bounds__(NT) k_adj_f64(AdjArgs a)
         for (; i < nt; ++i) {
             const uint32_t gi = gl + i;
             const int buf = gi % kStages;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else {
                 const Pix64 *sp = sbuf + buf * TP;
@@ -357,10 +354,7 @@ __global__ void __launch_bounds__(NT) k_adj_f64(AdjArgs a)
             if (tid == 0 && i + kStages < nt) issue_tile<Pix64, TP>(sbuf, bars, a.p64, p0 + i + kStages, gi + kStages);
         }
         if (s_abort) {
-            if (tid == 0) {
-                atomicOr(&a.st->bits, kStatTimeout);
-                drain<TP>(bars, gl, i, nt);
-            }
+            if (tid == 0) drain(bars, gl, i, i + kStages < nt ? i + kStages : nt, a.st);
             return;
         }
         gl += nt;

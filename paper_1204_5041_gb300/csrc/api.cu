@@ -36,9 +36,11 @@ int cuda_err(isw_ctx *c, cudaError_t e, const char *where)
                    cudaGetErrorString(e));
 }
 
-// A device-accessible pointer: device or managed memory.  Host (even pinned) pointers are
-// rejected because the kernels would read them over the bus or fault.
-bool is_device_ptr(const void *p)
+// A pointer the context's kernels may read: device memory of the context's own GPU, or managed
+// memory.  Host (even pinned) pointers are rejected because the kernels would read them over the
+// bus or fault, and so is device memory of another GPU (no peer mapping is set up: a kernel
+// reading it would fault).
+bool is_device_ptr(const isw_ctx *c, const void *p)
 {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -46,7 +48,8 @@ bool is_device_ptr(const void *p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == c->device;
 }
 
 void drop_graph(isw_ctx *c)
@@ -98,8 +101,8 @@ int check_pixels(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const in
     const int64_t all = 12 * nside * nside;
     if (npix < 0) return set_err(c, ISW_EINVAL, "npix < 0");
     if (pix_list) {
-        if (npix > 0 && !is_device_ptr(pix_list)) return set_err(c, ISW_EINVAL, "pix_list is not a device pointer");
-    } else if (pix0 < 0 || pix0 + npix > all) {
+        if (npix > 0 && !is_device_ptr(c, pix_list)) return set_err(c, ISW_EINVAL, "pix_list is not a device pointer of the context's GPU");
+    } else if (pix0 < 0 || pix0 > all || npix > all - pix0) {
         return set_err(c, ISW_EINVAL, "pixel range [%lld, %lld) outside [0, %lld)", (long long)pix0,
                        (long long)(pix0 + npix), (long long)all);
     }
@@ -110,7 +113,7 @@ int check_samples(isw_ctx *c, const double *samples, int64_t n, int64_t ld)
 {
     if (n < 0) return set_err(c, ISW_EINVAL, "n < 0");
     if (n > 0 && ld < n) return set_err(c, ISW_EINVAL, "ld (%lld) < n (%lld)", (long long)ld, (long long)n);
-    if (n > 0 && !is_device_ptr(samples)) return set_err(c, ISW_EINVAL, "samples is not a device pointer");
+    if (n > 0 && !is_device_ptr(c, samples)) return set_err(c, ISW_EINVAL, "samples is not a device pointer");
     return ISW_OK;
 }
 
@@ -137,14 +140,16 @@ PixelPlan plan_pixels(int64_t N, int64_t pix0, int64_t npix, const int64_t *pix_
     return p;
 }
 
+}  // namespace
+
 // Number of segment chunks: enough work items to fill every resident CTA slot with
-// near-equal waves, at least two segment tiles per chunk.
-int choose_split(int64_t ntiles, int64_t nst, int slots)
+// near-equal waves, at least two segment tiles per chunk, at most max_split chunks.
+int isw::choose_split(int64_t ntiles, int64_t nst, int slots, int max_split)
 {
     const double ideal = (double)ntiles / slots;
     int best = 1;
     double best_t = 1e300;
-    for (int k = 1; k <= 64; ++k) {
+    for (int k = 1; k <= 64 && k <= max_split; ++k) {
         if (k > 1 && nst / k < 2) break;
         const int64_t items = ntiles * k;
         const double waves = (double)((items + slots - 1) / slots);
@@ -157,6 +162,8 @@ int choose_split(int64_t ntiles, int64_t nst, int slots)
     }
     return best;
 }
+
+namespace {
 
 // Events around a pair-kernel launch when timing is on; returns the slot or -1.
 int timing_begin(isw_ctx *c, cudaStream_t s)
@@ -211,7 +218,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     const int64_t n_pad = (n + S - 1) / S * S;
     const int64_t nst = n_pad / S;
     const int slots = prec == ISW_F32C ? map_f32c_slots(vidx, c->num_sms) : map_f64_slots(c->num_sms);
-    const int split = c->split_override > 0 ? c->split_override : choose_split(pp.ntiles, nst, slots);
+    const int split = c->split_override > 0 ? c->split_override : choose_split(pp.ntiles, nst, slots, 64);
     int r;
     if ((r = ensure_ws(c, kWsNv, (size_t)pp.tot * 3 * sizeof(double)))) return r;
     if ((r = ensure_ws(c, kWsOut, (size_t)pp.tot * sizeof(int64_t)))) return r;
@@ -262,6 +269,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.accumulate = accumulate;
     a.st = c->d_status;
     a.queue = (unsigned long long *)c->ws[kWsQueue];
+    a.wait_polls = c->wait_polls;
     // timing a variant: every k-th pixel tile (all its segment chunks), about tune_waves waves
     a.tile_stride = 1;
     if (tune_waves > 0) {
@@ -314,6 +322,7 @@ int isw_create(isw_ctx **out, int device)
     c->d_far = 0.25;
     c->split_override = 0;
     c->tile_override = -1;
+    c->wait_polls = kWaitPolls;
     c->tuned_nside = -1;
     c->last_variant = -1;
     c->meta_nshell = -1;
@@ -380,6 +389,15 @@ int isw_set_param(isw_ctx *c, int key, double value)
         if (!(value >= -1.0 && value < num_f32_variants())) return set_err(c, ISW_EINVAL, "variant out of range");
         c->tile_override = (int)value;
         return ISW_OK;
+    case ISW_PARAM_WAIT_POLLS:
+        if (value < 0.0) {
+            c->wait_polls = kWaitPolls;
+            return ISW_OK;
+        }
+        if (!(value <= 2147483648.0) || value != std::floor(value))
+            return set_err(c, ISW_EINVAL, "wait polls must be an integer in [0, 2^31] (or < 0 for the default)");
+        c->wait_polls = (uint32_t)value;
+        return ISW_OK;
     default:
         return set_err(c, ISW_EINVAL, "unknown parameter key %d", key);
     }
@@ -396,6 +414,7 @@ int isw_get_param(const isw_ctx *c, int key, double *value)
     case ISW_PARAM_TIMING: *value = c->timing; return ISW_OK;
     case ISW_PARAM_D_FAR: *value = c->d_far; return ISW_OK;
     case ISW_PARAM_NUM_VARIANTS: *value = num_f32_variants(); return ISW_OK;
+    case ISW_PARAM_WAIT_POLLS: *value = c->wait_polls; return ISW_OK;
     default: return ISW_EINVAL;
     }
 }
@@ -424,6 +443,18 @@ int isw_get_timing(isw_ctx *c, double *ms, int64_t *pair_launches, int64_t *all_
     return ISW_OK;
 }
 
+int isw_fma_rate(isw_ctx *c, int prec, double *flop_per_s, void *stream)
+{
+    if (!c || !flop_per_s) return ISW_EINVAL;
+    if (prec != ISW_F64 && prec != ISW_F32C) return set_err(c, ISW_EINVAL, "unknown precision %d", prec);
+    int r;
+    if ((r = set_device(c))) return r;
+    if ((r = ensure_ws(c, kWsMisc, sizeof(double)))) return r;
+    r = fma_probe(prec == ISW_F64, c->num_sms, (double *)c->ws[kWsMisc], flop_per_s, (cudaStream_t)stream);
+    if (r) return set_err(c, r, "FMA throughput probe failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return ISW_OK;
+}
+
 int isw_check_status(isw_ctx *c, void *stream, int64_t *counts)
 {
     if (!c) return ISW_EINVAL;
@@ -440,7 +471,9 @@ int isw_check_status(isw_ctx *c, void *stream, int64_t *counts)
         counts[1] = (int64_t)h.domain_segs;
         counts[2] = (int64_t)h.near_pairs;
     }
-    if (h.bits & kStatTimeout) return set_err(c, ISW_ETIMEOUT, "a bounded device wait ran out");
+    if (h.bits & kStatDrain)
+        return set_err(c, ISW_ETIMEOUT, "a bounded device wait ran out, and so did the wait for a block's copies in flight");
+    if (h.bits & kStatTimeout) return set_err(c, ISW_ETIMEOUT, "a bounded device wait ran out (the map is incomplete)");
     if (h.bits & kStatNoConv) return set_err(c, ISW_ENOCONV, "a light-cone solve hit its iteration cap");
     if (h.bits & kStatBadIndex) return set_err(c, ISW_EINVAL, "a loop id or pixel index was out of range");
     if (h.bits & kStatDomain) return set_err(c, ISW_EDOMAIN, "a sample had 1 - Xdot^2 <= 0 or a non-finite weight");
@@ -455,7 +488,7 @@ int hp_pix2vec_ring(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     if ((r = check_pixels(c, nside, pix0, npix, pix_list))) return r;
     if (npix == 0) return ISW_OK;
     if (ld_out < npix) return set_err(c, ISW_EINVAL, "ld_out < npix");
-    if (!is_device_ptr(vec_out)) return set_err(c, ISW_EINVAL, "vec_out is not a device pointer");
+    if (!is_device_ptr(c, vec_out)) return set_err(c, ISW_EINVAL, "vec_out is not a device pointer");
     if ((r = set_device(c))) return r;
     launch_pix2vec(nside, pix0, npix, pix_list, vec_out, ld_out, c->d_status, (cudaStream_t)stream);
     c->n_launch += 1;
@@ -472,12 +505,12 @@ int lightcone_intersect(isw_ctx *c, int mode, const double *nodes_in, int64_t n,
     if ((r = check_samples(c, nodes_in, n, ld))) return r;
     if (n == 0) return ISW_OK;
     if (ld_out < n) return set_err(c, ISW_EINVAL, "ld_out < n");
-    if (!is_device_ptr(samples_out)) return set_err(c, ISW_EINVAL, "samples_out is not a device pointer");
-    if (tau_out && !is_device_ptr(tau_out)) return set_err(c, ISW_EINVAL, "tau_out is not a device pointer");
-    if (status && !is_device_ptr(status)) return set_err(c, ISW_EINVAL, "status is not a device pointer");
+    if (!is_device_ptr(c, samples_out)) return set_err(c, ISW_EINVAL, "samples_out is not a device pointer");
+    if (tau_out && !is_device_ptr(c, tau_out)) return set_err(c, ISW_EINVAL, "tau_out is not a device pointer");
+    if (status && !is_device_ptr(c, status)) return set_err(c, ISW_EINVAL, "status is not a device pointer");
     if (mode == ISW_LINEAR && !(t_obs > t_box)) return set_err(c, ISW_EINVAL, "t_obs must exceed t_box");
     if (mode == ISW_BURDEN) {
-        if (nloops <= 0 || ldp < nloops || !is_device_ptr(loop_params))
+        if (nloops <= 0 || ldp < nloops || !is_device_ptr(c, loop_params))
             return set_err(c, ISW_EINVAL, "BURDEN mode needs device loop_params[17][ldp], ldp >= nloops > 0");
     }
     if (!(std::isfinite(t_obs))) return set_err(c, ISW_EINVAL, "t_obs not finite");
@@ -501,14 +534,14 @@ int lightcone_adjoint(isw_ctx *c, int mode, const double *nodes_in, int64_t n, i
     if ((r = check_samples(c, nodes_in, n, ld))) return r;
     if (ngrad != 6 && ngrad != 9 && ngrad != 10) return set_err(c, ISW_EINVAL, "ngrad must be 6, 9 or 10");
     if (mode == ISW_BURDEN) {
-        if (nloops <= 0 || ldp < nloops || !is_device_ptr(loop_params))
+        if (nloops <= 0 || ldp < nloops || !is_device_ptr(c, loop_params))
             return set_err(c, ISW_EINVAL, "BURDEN mode needs device loop_params[17][ldp], ldp >= nloops > 0");
-        if (ld_gl < nloops || !is_device_ptr(grad_loops))
+        if (ld_gl < nloops || !is_device_ptr(c, grad_loops))
             return set_err(c, ISW_EINVAL, "BURDEN mode needs device grad_loops[17][ld_gl], ld_gl >= nloops");
     }
     if (n > 0) {
         if (ld_gs < n || ld_gn < n) return set_err(c, ISW_EINVAL, "ld_gs and ld_gn must be >= n");
-        if (!is_device_ptr(tau) || !is_device_ptr(grad_samples) || !is_device_ptr(grad_nodes))
+        if (!is_device_ptr(c, tau) || !is_device_ptr(c, grad_samples) || !is_device_ptr(c, grad_nodes))
             return set_err(c, ISW_EINVAL, "tau, grad_samples and grad_nodes must be device pointers");
     }
     if (mode == ISW_LINEAR && !std::isfinite(t_box)) return set_err(c, ISW_EINVAL, "t_box not finite");
@@ -541,7 +574,7 @@ int hp_vec2pix_ring(isw_ctx *c, int64_t nside, const double *vec, int64_t n, int
     if (n < 0) return set_err(c, ISW_EINVAL, "n < 0");
     if (n == 0) return ISW_OK;
     if (ld < n) return set_err(c, ISW_EINVAL, "ld < n");
-    if (!is_device_ptr(vec) || !is_device_ptr(pix_out)) return set_err(c, ISW_EINVAL, "vec and pix_out must be device pointers");
+    if (!is_device_ptr(c, vec) || !is_device_ptr(c, pix_out)) return set_err(c, ISW_EINVAL, "vec and pix_out must be device pointers");
     int r;
     if ((r = set_device(c))) return r;
     launch_vec2pix(nside, vec, n, ld, pix_out, c->d_status, (cudaStream_t)stream);
@@ -589,7 +622,7 @@ int box_place(isw_ctx *c, const double *nodes_box, int64_t ld_box, const int64_t
     const int64_t n_out = off[nshell];
     if (n_out == 0) return ISW_OK;
     if (ld_box < box_off[nbox] || ld_out < n_out) return set_err(c, ISW_EINVAL, "ld_box or ld_out too small");
-    if (!is_device_ptr(nodes_box) || !is_device_ptr(place) || !is_device_ptr(nodes_out))
+    if (!is_device_ptr(c, nodes_box) || !is_device_ptr(c, place) || !is_device_ptr(c, nodes_out))
         return set_err(c, ISW_EINVAL, "nodes_box, place and nodes_out must be device pointers");
     int r;
     if ((r = set_device(c))) return r;
@@ -624,8 +657,8 @@ int lightcone_intersect_shells(isw_ctx *c, const double *nodes, int64_t ld, cons
     int r;
     if ((r = check_samples(c, nodes, n, ld))) return r;
     if (n == 0) return ISW_OK;
-    if (ld_out < n || !is_device_ptr(samples_out)) return set_err(c, ISW_EINVAL, "samples_out: device, ld_out >= n");
-    if (burden && (nloops <= 0 || ldp < nloops || !is_device_ptr(loop_params)))
+    if (ld_out < n || !is_device_ptr(c, samples_out)) return set_err(c, ISW_EINVAL, "samples_out: device, ld_out >= n");
+    if (burden && (nloops <= 0 || ldp < nloops || !is_device_ptr(c, loop_params)))
         return set_err(c, ISW_EINVAL, "BURDEN shells need device loop_params[17][ldp], ldp >= nloops > 0");
     if (!std::isfinite(t_obs)) return set_err(c, ISW_EINVAL, "t_obs not finite");
     if ((r = set_device(c))) return r;
@@ -656,9 +689,9 @@ int cone_cut(isw_ctx *c, const double *samples, int64_t ld, const int64_t *shell
     const int64_t n = shell_off[nshell];
     int r;
     if ((r = check_samples(c, samples, n, ld))) return r;
-    if (!is_device_ptr(cone_pix) || !is_device_ptr(r_lo) || !is_device_ptr(r_hi) || !is_device_ptr(shell_off_out))
+    if (!is_device_ptr(c, cone_pix) || !is_device_ptr(c, r_lo) || !is_device_ptr(c, r_hi) || !is_device_ptr(c, shell_off_out))
         return set_err(c, ISW_EINVAL, "cone_pix, r_lo, r_hi and shell_off_out must be device pointers");
-    if (n > 0 && (ld_out < n || !is_device_ptr(samples_out)))
+    if (n > 0 && (ld_out < n || !is_device_ptr(c, samples_out)))
         return set_err(c, ISW_EINVAL, "samples_out: device, ld_out >= n");
     if ((r = set_device(c))) return r;
     cudaStream_t s = (cudaStream_t)stream;
@@ -703,7 +736,7 @@ int isw_map_patch(isw_ctx *c, const double *frame, int64_t M, double width, cons
     if (approx != ISW_FULLSKY && approx != ISW_FLATSKY) return set_err(c, ISW_EINVAL, "unknown approximation %d", approx);
     int r;
     if ((r = check_samples(c, samples, n, ld))) return r;
-    if (!is_device_ptr(theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
+    if (!is_device_ptr(c, theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
     if (!std::isfinite(GU)) return set_err(c, ISW_EINVAL, "GU not finite");
     if ((r = set_device(c))) return r;
     cudaStream_t s = (cudaStream_t)stream;
@@ -727,7 +760,7 @@ int isw_map_patch(isw_ctx *c, const double *frame, int64_t M, double width, cons
     const int64_t ntiles = ((M + tx - 1) / tx) * ((M + ty - 1) / ty), tot = ntiles * tx * ty;
     const int64_t n_pad = (n + S - 1) / S * S, nst = n_pad / S;
     const int slots = flat_slots(f64, c->num_sms);
-    const int split = c->split_override > 0 ? c->split_override : choose_split(ntiles, nst, slots);
+    const int split = c->split_override > 0 ? c->split_override : choose_split(ntiles, nst, slots, 64);
     if ((r = ensure_ws(c, kWsNv, (size_t)tot * 3 * sizeof(double)))) return r;
     if ((r = ensure_ws(c, kWsOut, (size_t)tot * sizeof(int64_t)))) return r;
     if ((r = ensure_ws(c, kWsPcap, (size_t)ntiles * sizeof(float4)))) return r;
@@ -749,7 +782,8 @@ int isw_map_patch(isw_ctx *c, const double *frame, int64_t M, double width, cons
     cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_err(c, e, "cudaMemsetAsync(work counters)");
     launch_map_flat(f64, r32, r64, outidx, ntiles, nst, split, M, width / (double)M, theta_out,
-                    split > 1 ? (double *)c->ws[kWsPartial] : nullptr, accumulate, c->d_status, queue, grid, s);
+                    split > 1 ? (double *)c->ws[kWsPartial] : nullptr, accumulate, c->d_status, queue, c->wait_polls,
+                    grid, s);
     c->n_launch += 1;
     c->n_pair += 1;
     if (split > 1) {
@@ -772,7 +806,7 @@ int isw_map_cl(isw_ctx *c, int64_t nside, const double *theta, int64_t lmax, dou
     if (!c) return ISW_EINVAL;
     if (nside < 1 || nside > cl_max_nside()) return set_err(c, ISW_EINVAL, "nside must be in [1, %d]", cl_max_nside());
     if (lmax < 0 || lmax > 4 * nside) return set_err(c, ISW_EINVAL, "lmax must be in [0, 4 nside]");
-    if (!is_device_ptr(theta) || !is_device_ptr(cl) || (alm && !is_device_ptr(alm)))
+    if (!is_device_ptr(c, theta) || !is_device_ptr(c, cl) || (alm && !is_device_ptr(c, alm)))
         return set_err(c, ISW_EINVAL, "theta, cl (and alm when given) must be device pointers");
     int r;
     if ((r = set_device(c))) return r;
@@ -796,7 +830,7 @@ int isw_map(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_t
     if ((r = check_pixels(c, nside, pix0, npix, pix_list))) return r;
     if ((r = check_samples(c, samples, n, ld))) return r;
     if (prec != ISW_F64 && prec != ISW_F32C) return set_err(c, ISW_EINVAL, "unknown precision %d", prec);
-    if (npix > 0 && !is_device_ptr(theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
+    if (npix > 0 && !is_device_ptr(c, theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
     if (!std::isfinite(GU)) return set_err(c, ISW_EINVAL, "GU not finite");
     if ((r = set_device(c))) return r;
     return map_impl(c, nside, pix0, npix, pix_list, samples, n, ld, x_obs, GU, prec, accumulate, theta_out,
@@ -815,8 +849,8 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     if (ngrad != 6 && ngrad != 9 && ngrad != 10) return set_err(c, ISW_EINVAL, "ngrad must be 6, 9 or 10");
     if (n == 0) return ISW_OK;
     if (ld_g < n) return set_err(c, ISW_EINVAL, "ld_g < n");
-    if (!is_device_ptr(grad_out)) return set_err(c, ISW_EINVAL, "grad_out is not a device pointer");
-    if (npix > 0 && !is_device_ptr(dL_dtheta)) return set_err(c, ISW_EINVAL, "dL_dtheta is not a device pointer");
+    if (!is_device_ptr(c, grad_out)) return set_err(c, ISW_EINVAL, "grad_out is not a device pointer");
+    if (npix > 0 && !is_device_ptr(c, dL_dtheta)) return set_err(c, ISW_EINVAL, "dL_dtheta is not a device pointer");
     if (!std::isfinite(GU)) return set_err(c, ISW_EINVAL, "GU not finite");
     if ((r = set_device(c))) return r;
     cudaStream_t s = (cudaStream_t)stream;
@@ -834,7 +868,7 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     const int64_t n_pad = (n + NT - 1) / NT * NT;
     const int64_t nseg_tiles = n_pad / NT;
     const int slots = adj_slots(prec, ngrad, c->num_sms);
-    int split = c->split_override > 0 ? c->split_override : choose_split(nseg_tiles, pp.ntiles, slots);
+    int split = c->split_override > 0 ? c->split_override : choose_split(nseg_tiles, pp.ntiles, slots, 64);
     if (split > pp.ntiles) split = (int)pp.ntiles;
     if ((r = ensure_ws(c, kWsNv, (size_t)pp.tot * 3 * sizeof(double)))) return r;
     if ((r = ensure_ws(c, kWsOut, (size_t)pp.tot * sizeof(int64_t)))) return r;
@@ -885,6 +919,7 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     a.partial = split > 1 ? (double *)c->ws[kWsAdjPartial] : nullptr;
     a.st = c->d_status;
     a.queue = (unsigned long long *)c->ws[kWsQueue];
+    a.wait_polls = c->wait_polls;
     const int64_t items = nseg_tiles * split;
     const int grid = (int)(items < slots ? items : slots);
     const int ti = timing_begin(c, s);
@@ -919,8 +954,8 @@ int isw_map_batched(isw_ctx *c, int64_t nside, const double *nodes, int64_t ld, 
     }
     int r;
     if ((r = check_samples(c, nodes, n, ld))) return r;
-    if (!is_device_ptr(theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
-    if (has_burden && !(flags & ISW_SKIP_LIGHTCONE) && (nloops <= 0 || ldp < nloops || !is_device_ptr(loop_params)))
+    if (!is_device_ptr(c, theta_out)) return set_err(c, ISW_EINVAL, "theta_out is not a device pointer");
+    if (has_burden && !(flags & ISW_SKIP_LIGHTCONE) && (nloops <= 0 || ldp < nloops || !is_device_ptr(c, loop_params)))
         return set_err(c, ISW_EINVAL, "BURDEN shells need device loop_params[17][ldp], ldp >= nloops > 0");
     if (!std::isfinite(t_obs) || !std::isfinite(GU)) return set_err(c, ISW_EINVAL, "t_obs / GU not finite");
     if ((r = set_device(c))) return r;
@@ -1023,7 +1058,7 @@ int isw_map_batched(isw_ctx *c, int64_t nside, const double *nodes, int64_t ld, 
     auto mixv = [&key](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
     mixv((uint64_t)nside); mixv((uint64_t)(uintptr_t)nodes); mixv((uint64_t)ld); mixv((uint64_t)nshell);
     mixv((uint64_t)(uintptr_t)loop_params); mixv((uint64_t)nloops); mixv((uint64_t)ldp);
-    double dv[8] = {xo[0], xo[1], xo[2], t_obs, GU, c->near_k, c->b_min, c->d_far};
+    double dv[9] = {xo[0], xo[1], xo[2], t_obs, GU, c->near_k, c->b_min, c->d_far, (double)c->wait_polls};
     for (double d : dv) { uint64_t u; memcpy(&u, &d, 8); mixv(u); }
     mixv((uint64_t)prec); mixv((uint64_t)flags); mixv((uint64_t)accumulate); mixv((uint64_t)(uintptr_t)theta_out);
     mixv((uint64_t)c->split_override); mixv((uint64_t)(c->tile_override + 1)); mixv((uint64_t)c->auto_variant);

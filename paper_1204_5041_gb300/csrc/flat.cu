@@ -83,6 +83,7 @@ struct FlatArgs {
     int accumulate;
     DevStatus *st;
     unsigned long long *queue;
+    uint32_t wait_polls;
 };
 
 template <bool F64>
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kFlatNT) k_map_flat(FlatArgs a)
         for (; i < nt; ++i) {
             const uint32_t gi = g + i;
             const int buf = gi % kStages;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else {
                 const Rec *sb = sbuf + buf * S;
@@ -184,10 +185,7 @@ __global__ void __launch_bounds__(kFlatNT) k_map_flat(FlatArgs a)
             if (tid == 0 && i + kStages < nt) issue_tile<Rec, S>(sbuf, bars, src, j0 + i + kStages, gi + kStages);
         }
         if (s_abort) {
-            if (tid == 0) {
-                atomicOr(&a.st->bits, kStatTimeout);
-                drain<S>(bars, g, i, nt);
-            }
+            if (tid == 0) drain(bars, g, i, i + kStages < nt ? i + kStages : nt, a.st);
             return;
         }
         g += nt;
@@ -230,7 +228,7 @@ int flat_slots(bool f64, int num_sms)
 
 void launch_map_flat(bool f64, const void *r32, const void *r64, const int64_t *outidx, int64_t ntiles, int64_t nst,
                      int split, int64_t M, double pitch, double *theta, double *partial, int accumulate,
-                     DevStatus *st, unsigned long long *queue, int grid, cudaStream_t s)
+                     DevStatus *st, unsigned long long *queue, uint32_t wait_polls, int grid, cudaStream_t s)
 {
     FlatArgs a;
     a.r32 = (const Flat32 *)r32;
@@ -246,6 +244,7 @@ void launch_map_flat(bool f64, const void *r32, const void *r64, const int64_t *
     a.accumulate = accumulate;
     a.st = st;
     a.queue = queue;
+    a.wait_polls = wait_polls;
     const size_t sm = kStages * kFlatS * (f64 ? sizeof(Flat64) : sizeof(Flat32)) + kStages * sizeof(uint64_t);
     if (f64) k_map_flat<true><<<grid, kFlatNT, sm, s>>>(a);
     else k_map_flat<false><<<grid, kFlatNT, sm, s>>>(a);

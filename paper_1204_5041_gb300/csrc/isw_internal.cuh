@@ -285,11 +285,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait on phase `parity`; about 2^22 polls (each try_wait itself blocks for a
-// hardware-defined interval) before giving up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Limits of the bounded waits, in try_wait polls (each try_wait itself suspends the thread for
+// a hardware-defined interval while the phase is incomplete).  A consumer wait (a stage of
+// records or pixels the CTA is about to read) gives up after kWaitPolls by default
+// (ISW_PARAM_WAIT_POLLS overrides it); after a consumer wait ran out, the CTA waits for the
+// bulk copies it still has in flight with the separate, much longer kDrainPolls, so that it
+// does not exit while a copy into its shared memory is outstanding.
+constexpr uint32_t kWaitPolls = 1u << 22;
+constexpr uint32_t kDrainPolls = 1u << 26;
+
+// Bounded wait on phase `parity`: at most `polls` polls, then false (polls = 0 gives up at once).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t polls)
 {
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
+    for (uint32_t it = 0; it < polls; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
     }
     return false;
@@ -319,6 +327,7 @@ enum : uint32_t {
     kStatTimeout = 1u << 1,  // a bounded wait ran out
     kStatNoConv = 1u << 2,   // light-cone Newton iteration cap reached
     kStatBadIndex = 1u << 3, // a loop id or pixel index out of range
+    kStatDrain = 1u << 4,    // after a time-out, the wait for a CTA's copies in flight ran out too
 };
 
 struct DevStatus {
@@ -441,7 +450,7 @@ struct isw_ctx {
     double d_far;       // segment tiles this chord away from the pixel tile use the far-field form
     int split_override; // segment chunks for the forward maps (0 = automatic)
     int tile_override;  // FP32 kernel variant index (-1 = automatic)
-    int timeout_polls;  // reserved
+    uint32_t wait_polls; // limit of the kernels' consumer waits (ISW_PARAM_WAIT_POLLS)
     // pair-kernel timing (ISW_PARAM_TIMING)
     int timing;
     int n_timed;

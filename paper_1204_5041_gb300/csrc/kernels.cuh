@@ -5,6 +5,14 @@
 
 namespace isw {
 
+// api.cu: number of work chunks along the streamed axis for ntiles tiles of the other axis, nst
+// streamed tiles and `slots` resident CTAs (near-equal waves; at least two streamed tiles per
+// chunk; at most max_split chunks)
+int choose_split(int64_t ntiles, int64_t nst, int slots, int max_split);
+
+// probe.cu: FMA-pipe throughput (flop/s, FMA = 2) of the FP32 or FP64 pipe; sink is never written
+int fma_probe(bool f64, int num_sms, double *sink, double *flops, cudaStream_t s);
+
 // healpix.cu
 int launch_pix2vec(int64_t N, int64_t pix0, int64_t npix, const int64_t *pix_list, double *out, int64_t ld,
                    DevStatus *st, cudaStream_t s);
@@ -34,7 +42,7 @@ void launch_flat_pack(const double *S, int64_t n, int64_t ld, const PatchSpec &p
                       double GU, int64_t n_pad, void *r32, void *r64, cudaStream_t s);
 void launch_map_flat(bool f64, const void *r32, const void *r64, const int64_t *outidx, int64_t ntiles, int64_t nst,
                      int split, int64_t M, double pitch, double *theta, double *partial, int accumulate,
-                     DevStatus *st, unsigned long long *queue, int grid, cudaStream_t s);
+                     DevStatus *st, unsigned long long *queue, uint32_t wait_polls, int grid, cudaStream_t s);
 
 // cl.cu: angular power spectrum (F: double[2][4N-1][lmax+1] workspace; alm: double[2][lmax+1][lmax+1])
 int cl_max_nside();
@@ -99,6 +107,7 @@ struct MapArgs {
     DevStatus *st;
     int64_t tile_stride;     // 1; > 1 only when timing variants: every tile_stride-th pixel tile
     unsigned long long *queue;   // work counters (far pass or FP64 kernel, near pass), zero at launch
+    uint32_t wait_polls;     // limit of the consumer waits (kWaitPolls by default)
 };
 struct Variant {
     int threads, ppt, seg_tile, tx, ty;
@@ -134,6 +143,7 @@ struct AdjArgs {
     double *partial;         // [split][ngrad][n_pad] when split > 1
     DevStatus *st;
     unsigned long long *queue;   // work counter, zero at launch
+    uint32_t wait_polls;     // limit of the consumer waits (kWaitPolls by default)
 };
 int adj_seg_tile(int prec);
 int adj_pix_tile(int prec);

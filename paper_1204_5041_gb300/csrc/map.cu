@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
         for (; i < nt; ++i) {
             const uint32_t gi = g + i;
             const int buf = gi % kStages;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else if (s_cls[buf] == kFar) {
                 const ulonglong2 *fr = reinterpret_cast<const ulonglong2 *>(sbuf + (size_t)buf * S2);
@@ -138,10 +138,7 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
             if (tid == 0 && i + kStages < nt) issue(j0 + i + kStages, gi + kStages);
         }
         if (s_abort) {
-            if (tid == 0) {
-                atomicOr(&a.st->bits, kStatTimeout);
-                drain<S>(bars, g, i, nt);
-            }
+            if (tid == 0) drain(bars, g, i, i + kStages < nt ? i + kStages : nt, a.st);
             return;
         }
         g += nt;
@@ -250,7 +247,7 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
             const int buf = gi % kStages;
             // the stage's tile index is read before the barrier: warp 0 rewrites the slot after it
             int64_t j = -1;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else {
                 j = s_j[buf];
@@ -354,15 +351,15 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
             if (w == 0) issue_next(gi + kStages);
         }
         if (s_abort) {
-            if (tid == 0) atomicOr(&a.st->bits, kStatTimeout);
-            // every issued stage after this one was either a copy or a zero-byte arrive
-            if (tid == 0) drain<S>(bars, g, i, i + kStages);
+            // stages i .. i + kStages - 1 are issued: copies or zero-byte arrives
+            if (tid == 0) drain(bars, g, i, i + kStages, a.st);
             return;
         }
-        // stages issued after the end marker (zero-byte arrives) complete their phases; consume them
+        // stages issued after the end marker are zero-byte arrives, made before the last barrier:
+        // their phases are complete; consume them
         for (int m = i + 1; m < i + kStages; ++m) {
             const uint32_t gm = g + m;
-            (void)__all_sync(0xffffffffu, mbar_wait_bounded(&bars[gm % kStages], (gm / kStages) & 1));
+            (void)__all_sync(0xffffffffu, mbar_wait_bounded(&bars[gm % kStages], (gm / kStages) & 1, kDrainPolls));
         }
         __syncthreads();
         g += i + kStages;
@@ -438,7 +435,7 @@ __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
         for (; i < nt; ++i) {
             const uint32_t gi = g + i;
             const int buf = gi % kStages;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else {
                 const Seg64 *sb = sbuf + buf * S;
@@ -464,10 +461,7 @@ __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
             if (tid == 0 && i + kStages < nt) issue_tile<Seg64, S>(sbuf, bars, a.s64, j0 + i + kStages, gi + kStages);
         }
         if (s_abort) {
-            if (tid == 0) {
-                atomicOr(&a.st->bits, kStatTimeout);
-                drain<S>(bars, g, i, nt);
-            }
+            if (tid == 0) drain(bars, g, i, i + kStages < nt ? i + kStages : nt, a.st);
             return;
         }
         g += nt;

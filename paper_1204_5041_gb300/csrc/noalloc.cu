@@ -11,7 +11,11 @@
 // Every GPU that loads the library holds that array until the process exits.  All calls
 // share it and it keeps the previous call's contents: each call clears the status word and
 // overwrites every other byte it reads, and two calls that overlap on the GPU (different
-// streams, no ordering between them) race on it and give wrong maps.
+// streams, no ordering between them) race on it and give wrong maps.  The launch sequence,
+// kernel variant and segment-chunk rule are those of isw_map with default settings (the chunk
+// count is capped by the scratch left), so within that cap the map equals isw_map's bit for bit.
+// A caller that passes status_out gets the status the kernels recorded (skipped samples, a
+// bounded wait that ran out), read back after a stream synchronisation.
 #include <cmath>
 #include <mutex>
 
@@ -32,14 +36,26 @@ int g_num_sms[kMaxDevices];
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-bool device_ptr(const void *p)
+// Device memory of GPU `dev` (the current device), or managed memory: the kernels of this call
+// run on `dev` and would fault on a host pointer or on another GPU's memory.
+bool device_ptr(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// Device-side conditions recorded in the status word, as a status code (time-outs first).
+int status_code(const DevStatus &h)
+{
+    if (h.bits & (kStatTimeout | kStatDrain)) return ISW_ETIMEOUT;
+    if (h.bits & kStatBadIndex) return ISW_EINVAL;
+    if (h.bits & kStatDomain) return ISW_EDOMAIN;
+    return ISW_OK;
 }
 
 // One-time set-up per device (the device must be current): the device address of the
@@ -68,20 +84,27 @@ int scratch_address(int dev, void **addr, int *sms)
 }  // namespace
 
 extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, const double *samples, int64_t n,
-                                    int64_t ld, const double *x_obs, double GU, double *theta_out, void *stream)
+                                    int64_t ld, const double *x_obs, double GU, double *theta_out, int32_t *status_out,
+                                    void *stream)
 {
+    if (status_out) *status_out = ISW_OK;
     // ---- host-side checks (nothing is enqueued when they fail)
     if (nside < 1 || nside > (1 << 24)) return ISW_EINVAL;
     const int64_t all = 12 * nside * nside;
-    if (npix < 0 || pix0 < 0 || pix0 + npix > all || n < 0 || (n > 0 && ld < n)) return ISW_EINVAL;
+    if (pix0 < 0 || pix0 > all || npix < 0 || npix > all - pix0 || n < 0 || (n > 0 && ld < n)) return ISW_EINVAL;
     if (npix == 0) return ISW_OK;
     if (!theta_out || (n > 0 && !samples)) return ISW_EINVAL;
-    if (!device_ptr(theta_out) || (n > 0 && !device_ptr(samples))) return ISW_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return ISW_ECUDA;
+    }
+    if (!device_ptr(theta_out, dev) || (n > 0 && !device_ptr(samples, dev))) return ISW_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     if (n == 0) return cudaMemsetAsync(theta_out, 0, (size_t)npix * sizeof(double), s) == cudaSuccess ? ISW_OK
                                                                                                          : ISW_ECUDA;
 
-    // ---- scratch layout for the FP32 pair kernel's first variant
+    // ---- scratch layout for the FP32 pair kernel's first variant (the one isw_map uses by default)
     const Variant v = f32_variant(0);
     const int S = v.seg_tile, tile = v.tx * v.ty;
     const bool full = (pix0 == 0 && npix == all);
@@ -102,28 +125,17 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     const size_t off_far = at; at += up256((size_t)(n_pad / 2) * sizeof(Far2));
     off[7] = at;
     if (at > kStaticScratchBytes) return ISW_EINVAL;  // problem too large for the static scratch
+    // segment-chunk partials fit for at most `room` chunks
     const int64_t room = (int64_t)((kStaticScratchBytes - at) / ((size_t)tot * sizeof(double)));
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ISW_ECUDA;
     void *base = nullptr;
     int sms = 0;
     int r = scratch_address(dev, &base, &sms);
     if (r) return r;
 
-    // segment chunks: fill the resident CTA slots in near-equal waves, within the scratch left
+    // segment chunks: the rule isw_map uses, capped by the scratch left
     const int slots = map_f32c_slots(0, sms);
-    int split = 1;
-    double best = 1e300;
-    for (int k = 1; k <= 64 && k <= room; ++k) {
-        if (k > 1 && nst / k < 2) break;
-        const double t = (double)((ntiles * k + slots - 1) / slots) / k;
-        if (t < best * 0.98) {
-            best = t;
-            split = k;
-        }
-    }
-
+    const int split = choose_split(ntiles, nst, slots, (int)(room < 64 ? room : 64));
     unsigned char *b = (unsigned char *)base;
     DevStatus *st = (DevStatus *)(b + off[0]);
     double *nv = (double *)(b + off[1]);
@@ -165,9 +177,21 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.st = st;
     a.tile_stride = 1;
     a.queue = queue;
+    a.wait_polls = kWaitPolls;
     const int64_t items = ntiles * split;
     launch_map_f32c(0, a, (int)(items < slots ? items : slots), s);
     launch_map_f32c_near(0, a, sms, s);
     if (split > 1) launch_reduce_partials(a, tile, s);
-    return cudaGetLastError() == cudaSuccess ? ISW_OK : ISW_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return ISW_ECUDA;
+    if (status_out) {
+        // what the kernels recorded: wait for them, then read the status word (no allocation)
+        DevStatus h;
+        if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return ISW_ECUDA;
+        }
+        *status_out = status_code(h);
+    }
+    return ISW_OK;
 }

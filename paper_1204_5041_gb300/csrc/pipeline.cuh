@@ -51,14 +51,20 @@ __device__ __forceinline__ void issue_tile(Rec *sbuf, uint64_t *bars, const Rec 
     bulk_g2s(sbuf + b * S, src + j * S, (uint32_t)(S * sizeof(Rec)), &bars[b]);
 }
 
-// After a timeout: wait (bounded) for every copy still in flight before leaving the CTA.
-template <int S>
-__device__ __forceinline__ void drain(uint64_t *bars, uint32_t g, int i, int nt)
+// After a consumer wait ran out (one thread): record the time-out, then wait for the stages
+// i .. last-1 of this item, issued and not yet consumed, so that no bulk copy into this CTA's
+// shared memory is still in flight when it exits.  These waits have their own limit
+// (kDrainPolls), independent of the consumer limit; if one runs out as well, kStatDrain is
+// recorded (the host reports it as a time-out with a copy possibly outstanding).
+__device__ __forceinline__ void drain(uint64_t *bars, uint32_t g, int i, int last, DevStatus *st)
 {
-    const int last = (i + kStages < nt) ? i + kStages : nt;
+    atomicOr(&st->bits, kStatTimeout);
     for (int m = i; m < last; ++m) {
         const uint32_t gm = g + m;
-        (void)mbar_wait_bounded(&bars[gm % kStages], (gm / kStages) & 1);
+        if (!mbar_wait_bounded(&bars[gm % kStages], (gm / kStages) & 1, kDrainPolls)) {
+            atomicOr(&st->bits, kStatDrain);
+            return;
+        }
     }
 }
 

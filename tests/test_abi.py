@@ -18,7 +18,8 @@ def test_header_declares_the_boundary():
     for n in ("hp_pix2vec_ring", "lightcone_intersect", "isw_map", "isw_map_adjoint", "isw_map_batched",
               "isw_create", "isw_destroy", "isw_last_error", "isw_check_status", "isw_set_param",
               "isw_get_param", "isw_get_timing", "lightcone_adjoint", "hp_vec2pix_ring", "box_place",
-              "lightcone_intersect_shells", "cone_cut", "isw_map_patch", "isw_map_cl", "isw_map_f32c_noalloc"):
+              "lightcone_intersect_shells", "cone_cut", "isw_map_patch", "isw_map_cl", "isw_map_f32c_noalloc",
+              "isw_fma_rate"):
         assert n in names
 
 

@@ -1,5 +1,6 @@
 """GPU parity of isw_map_cl (Fig. 4: the angular power spectrum of the map) against the oracle:
-a_lm within 1e-10 of max|a_lm| and C_l within 1e-9 relative, on a string map and a random map."""
+a_lm within 1e-10 of max|a_lm| and C_l within 1e-9 relative, on string maps and white-noise maps,
+from N_side 1 up to the sizes the benchmark quotes (N_side 512 and 1024, l_max 1536)."""
 import os
 
 import numpy as np
@@ -44,6 +45,55 @@ def test_cl_vs_oracle(isw, N, lmax):
     ec = np.max(np.abs(cl - ref_cl) / (np.abs(ref_cl) + 1e-12 * ref_cl.max()))
     print(f"cl N={N} lmax={lmax}: alm err {ea:.3e}, cl err {ec:.3e}")
     assert ea <= 1e-10 and ec <= 1e-9
+
+
+def _m_subset(lmax, step):
+    """Every step-th m plus the edges of the kernel's 512-wide coefficient chunks and lmax."""
+    ms = set(range(0, lmax + 1, step)) | {1, 2, lmax - 1, lmax}
+    for e in (511, 512, 513, 1023, 1024, 1025):
+        if e <= lmax:
+            ms.add(e)
+    return sorted(ms)
+
+
+@pytest.mark.parametrize("N,lmax,kind,mstep", [
+    (256, 767, "strings", 1),     # two ring pairs per thread, two coefficient chunks; all m
+    (512, 1536, "noise", 1),      # four ring pairs per thread, four chunks (l = m .. 1536); all m
+    (1024, 1536, "noise", 48),    # eight ring pairs per thread (the kernel's maximum); a subset of m
+])
+def test_cl_vs_oracle_bench_sizes(isw, N, lmax, kind, mstep):
+    """The sizes the benchmark quotes C_l at: several 512-l coefficient chunks, several ring pairs
+    per thread, and (white noise) power up to l_max at every m, so that lambda_lm underflows near
+    the poles for large m and the exponent tracking decides the result."""
+    if kind == "strings":
+        w = synth.config(0, seed=2)
+        S, _, st = oracle.lightcone_workload(w)
+        assert np.all(st == 0)
+        theta = isw.isw_map(N, _d(S), prec="f64").cpu().numpy()
+    else:
+        theta = np.random.default_rng(N + 7).normal(size=12 * N * N)
+    alm, cl = isw.isw_map_cl(N, _d(theta), lmax, with_alm=True)
+    alm, cl = alm.cpu().numpy(), cl.cpu().numpy()
+    if mstep == 1:
+        ref_a, ref_cl = oracle.map_alm_cl(N, theta, lmax, threads=THREADS)
+        ea = np.max(np.abs(alm - ref_a)) / np.max(np.abs(ref_a))
+        ec = np.max(np.abs(cl - ref_cl) / (np.abs(ref_cl) + 1e-12 * ref_cl.max()))
+        print(f"cl N={N} lmax={lmax} ({kind}, all m): alm err {ea:.3e}, cl err {ec:.3e}")
+        assert ec <= 1e-9
+    else:
+        ms = _m_subset(lmax, mstep)
+        ref = oracle.map_alm_m(N, theta, lmax, ms, threads=THREADS)
+        got = alm[ms]
+        ref_a = ref[0] + 1j * ref[1]
+        ea = np.max(np.abs(got - ref_a)) / np.max(np.abs(ref_a))
+        print(f"cl N={N} lmax={lmax} ({kind}, {len(ms)} values of m): alm err {ea:.3e}")
+    assert ea <= 1e-10
+    # every coefficient of a white-noise map is of the same order: none may vanish by underflow
+    if kind == "noise":
+        rows = alm if mstep == 1 else alm[_m_subset(lmax, mstep)]
+        ms = np.arange(lmax + 1) if mstep == 1 else np.array(_m_subset(lmax, mstep))
+        for r, m in zip(rows, ms):
+            assert np.all(np.abs(r[m:]) > 0.0), m
 
 
 def test_cl_argument_errors(isw):
