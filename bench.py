@@ -558,6 +558,9 @@ def run_case(args):
     cfg = {"map_f64": 0, "adjoint_f32c": 3, "adjoint_f64": 3, "map_f32c": 1}[args.case]
     w = synth.config(cfg, seed=args.seed)
     nside = args.nside or {0: 64, 3: 128, 1: 128}[cfg]
+    ctx = isw.default_context(0)
+    if args.d_far is not None:
+        ctx.set_param(isw.PARAM_D_FAR, args.d_far)
     nodes = torch.from_numpy(np.ascontiguousarray(w.nodes)).to(dev)
     loops = torch.from_numpy(np.ascontiguousarray(w.loop_params)).to(dev)
     samples = isw.lightcone_intersect_shells(nodes, w.shell_off, w.t_box, w.mode, loops, x_obs=w.x_obs,
@@ -582,11 +585,12 @@ def run_case(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    r, _ = isw.default_context(0).check_status()
+    r, counts = ctx.check_status()
     if r != isw.OK:
         raise RuntimeError(f"device status {r}")
     print(f"case {args.case}: Nside={nside} ({npix} pixels) x {w.n} samples = {npix * w.n:.3e} pairs, "
-          f"{ms:.3f} ms per call, {npix * w.n / (ms / 1e3):.3e} pairs/s")
+          f"{ms:.3f} ms per call, {npix * w.n / (ms / 1e3):.3e} pairs/s, d_far {ctx.get_param(isw.PARAM_D_FAR)}, "
+          f"near pairs per call {counts['near_pairs'] / max(args.warmup + args.steps, 1):.3e}")
 
 
 def main():

@@ -16,7 +16,12 @@
 //
 // Work items are (tile of NT samples, chunk of pixel tiles): one thread per sample, pixel
 // records of a tile staged in shared memory by 1-D bulk copies and read by every thread.
-// Per-chunk gradients are reduced over chunks in a fixed order (deterministic).
+// FP32 kernel: a pixel tile whose bounding cap is at least d_far from the sample tile's cap (and
+// outside its beam cap) is staged as pixel-pair records and summed by a packed f32x2 loop, two
+// pixels per instruction, from the far-field form of the sums (adj_far_stage: 33 FP32 lane
+// operations and two reciprocals per pair); other tiles go through the checked loop (float-pair
+// d, cancellation-free B, FP64 for near pairs).  Per-chunk gradients are reduced over chunks in a
+// fixed order (deterministic).
 #include "isw_internal.cuh"
 #include "kernels.cuh"
 #include "pipeline.cuh"
@@ -132,7 +137,7 @@ __device__ __forceinline__ void adj_assemble(const Seg64 &s, const double *acc, 
 
 __global__ void k_pack_pixels(const double *__restrict__ nv, int64_t ldn, const int64_t *__restrict__ outidx,
                               const double *__restrict__ g, int64_t tot, Pix32 *__restrict__ p32,
-                              Pix64 *__restrict__ p64)
+                              Pix64 *__restrict__ p64, PixF2 *__restrict__ pf2)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < tot; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t oi = outidx[k];
@@ -150,20 +155,168 @@ __global__ void k_pack_pixels(const double *__restrict__ nv, int64_t ldn, const 
             hi[c] = __double2float_rn(d.n[c]);
             lo[c] = __double2float_rn(d.n[c] - (double)hi[c]);
         }
-        f.a = make_float4(hi[0], hi[1], hi[2], __double2float_rn(d.g));
+        const float gf = __double2float_rn(d.g);
+        f.a = make_float4(hi[0], hi[1], hi[2], gf);
         f.b = make_float4(lo[0], lo[1], lo[2], 0.f);
         p32[k] = f;
         p64[k] = d;
+        // pixel k is half (k & 1) of pair k / 2
+        float *fp = reinterpret_cast<float *>(pf2 + k / 2) + (k & 1);
+        fp[0] = hi[0];
+        fp[2] = hi[1];
+        fp[4] = hi[2];
+        fp[6] = gf;
     }
 }
 
-template <int NT, int TP, bool NG9>
-__global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
+// Far-field loop of the FP32 adjoint over one stage of pixel-pair records (|d| >= d_far and
+// B >= b_min for every pair of the tile pair), two pixels per packed f32x2 operation.  Per pair,
+// with d = n - Xhat, Q = d.d, A = n.X', B = 1 + n.Xdot, Xdot.d = B - e and X'.d = A - f
+// (e = 1 + Xdot.Xhat, f = X'.Xhat from the sample record) and N = B Xdot.d - A X'.d (so that
+// the pair's T = N / (BQ)):
+//   gq = g/Q,  ga = gq A/B,  gT = g N/(BQ),  ge = gT/Q,  w = gq + ga (X'.d)/B,  [u = ga + gq (X'.d)/B]
+// and the partial sums  S2 = sum gq, S3 = sum ga, S4 = sum gT, V1 = sum ge d, V2 = sum w n
+// [V3 = sum u n]; the signs of N, gT, ge are carried negated so that every step is a plain
+// packed multiply or multiply-add: 33 FP32 lane operations and two reciprocals per pair (ngrad 6).
+// Per window of 32 pixel pairs the partials are converted into the accumulator layout of the
+// checked loop (adj_pair32): acc0 += (e - 1) S2 - f S3, acc1 += S2, acc2 += S3, acc3 += S4,
+// acc4..6 += 2 V1, acc7..9 += V2 - S2 Xhat, acc10..12 += V3 - S3 Xhat  (|d| >= d_far bounds the
+// cancellation of the last two by 1/d_far), and folded into the compensated (hi, lo) pairs.
+template <int TP, bool NG9>
+__device__ __forceinline__ void adj_far_stage(const ulonglong2 *__restrict__ fr, const Seg32 &r, float *ahi,
+                                              float *alo)
 {
+    constexpr int kWin = 32, NP = NG9 ? 12 : 9;
+    const uint64_t one2 = f2_pack(1.f, 1.f);
+    const uint64_t cx = f2_pack(r.a.x, r.a.x), cy = f2_pack(r.a.y, r.a.y), cz = f2_pack(r.a.z, r.a.z);
+    const uint64_t dx0 = f2_pack(r.d.x, r.d.x), dy0 = f2_pack(r.d.y, r.d.y), dz0 = f2_pack(r.d.z, r.d.z);
+    const uint64_t px0 = f2_pack(r.e.x, r.e.x), py0 = f2_pack(r.e.y, r.e.y), pz0 = f2_pack(r.e.z, r.e.z);
+    const uint64_t ce = f2_pack(r.d.w, r.d.w), cf = f2_pack(r.e.w, r.e.w);
+    for (int w0 = 0; w0 < TP / 2; w0 += kWin) {
+        uint64_t ps[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) ps[k] = 0ull;
+#pragma unroll 4
+        for (int q = w0; q < w0 + kWin; ++q) {
+            const ulonglong2 ra = fr[2 * q], rb = fr[2 * q + 1];
+            const uint64_t nx = ra.x, ny = ra.y, nz = rb.x, g = rb.y;
+            const uint64_t dx = f2_sub(nx, cx), dy = f2_sub(ny, cy), dz = f2_sub(nz, cz);
+            const uint64_t Q = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+            const uint64_t A = f2_fma(nz, pz0, f2_fma(ny, py0, f2_mul(nx, px0)));
+            const uint64_t B = f2_fma(nz, dz0, f2_fma(ny, dy0, f2_fma(nx, dx0, one2)));
+            const uint64_t Qd = f2_sub(A, cf);                             // X'.d
+            const uint64_t Nn = f2_fma(B, f2_sub(ce, B), f2_mul(A, Qd));   // -N
+            float q0, q1, b0, b1;
+            f2_unpack(Q, q0, q1);
+            f2_unpack(B, b0, b1);
+            const uint64_t iQ = f2_pack(rcp_approx(q0), rcp_approx(q1));
+            const uint64_t iB = f2_pack(rcp_approx(b0), rcp_approx(b1));
+            const uint64_t gq = f2_mul(g, iQ);
+            const uint64_t ga = f2_mul(gq, f2_mul(A, iB));
+            const uint64_t gTn = f2_mul(Nn, f2_mul(gq, iB));               // -gT
+            const uint64_t gen = f2_mul(gTn, iQ);                          // -ge
+            const uint64_t t1 = f2_mul(Qd, iB);
+            const uint64_t w = f2_fma(ga, t1, gq);
+            ps[0] = f2_add(ps[0], gq);
+            ps[1] = f2_add(ps[1], ga);
+            ps[2] = f2_add(ps[2], gTn);
+            ps[3] = f2_fma(gen, dx, ps[3]);
+            ps[4] = f2_fma(gen, dy, ps[4]);
+            ps[5] = f2_fma(gen, dz, ps[5]);
+            ps[6] = f2_fma(w, nx, ps[6]);
+            ps[7] = f2_fma(w, ny, ps[7]);
+            ps[8] = f2_fma(w, nz, ps[8]);
+            if (NG9) {
+                const uint64_t u = f2_fma(gq, t1, ga);
+                ps[9] = f2_fma(u, nx, ps[9]);
+                ps[10] = f2_fma(u, ny, ps[10]);
+                ps[11] = f2_fma(u, nz, ps[11]);
+            }
+        }
+        float v[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float lo, hi;
+            f2_unpack(ps[k], lo, hi);
+            v[k] = lo + hi;
+        }
+        const float xh[3] = {r.a.x, r.a.y, r.a.z};
+        fold(ahi[0], alo[0], fmaf(r.d.w - 1.f, v[0], -r.e.w * v[1]));
+        fold(ahi[1], alo[1], v[0]);
+        fold(ahi[2], alo[2], v[1]);
+        fold(ahi[3], alo[3], -v[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            fold(ahi[4 + c], alo[4 + c], -2.f * v[3 + c]);
+            fold(ahi[7 + c], alo[7 + c], fmaf(-v[0], xh[c], v[6 + c]));
+            if (NG9) fold(ahi[10 + c], alo[10 + c], fmaf(-v[1], xh[c], v[9 + c]));
+        }
+    }
+}
+
+// Checked loop of the FP32 adjoint over one stage of Pix32 records: d as a float pair, B formed
+// without cancellation, pairs with |d| < rho or B < b_min / 1000 in FP64 from the FP64 records.
+template <int TP, bool NG9>
+__device__ __forceinline__ void adj_checked_stage(const Pix32 *__restrict__ sp, const Seg32 &r, const AdjArgs &a,
+                                                  int64_t pt, int64_t s, int NG, float *ahi, float *alo,
+                                                  unsigned &nearcnt, unsigned &zerocnt)
+{
+    const float em1 = r.d.w - 1.f;   // Xdot.Xhat
+    const float hv = fmaf(-0.5f, r.k.w, 0.5f);
+    const float b_tiny = a.b_min * 1e-3f;
+    // FP32 partial sums over windows of 32 pixels, folded into compensated (hi, lo) pairs
+    for (int w0 = 0; w0 < TP; w0 += 32) {
+        float part[kAcc];
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) part[k] = 0.f;
+        for (int q = w0; q < w0 + 32; ++q) {
+            const float4 pa = sp[q].a, pb = sp[q].b;
+            const float dx = (pa.x - r.a.x) + (pb.x - r.b.x);
+            const float dy = (pa.y - r.a.y) + (pb.y - r.b.y);
+            const float dz = (pa.z - r.a.z) + (pb.z - r.b.z);
+            const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float Pd = fmaf(r.d.z, dz, fmaf(r.d.y, dy, r.d.x * dx));
+            const float Qd = fmaf(r.e.z, dz, fmaf(r.e.y, dy, r.e.x * dx));
+            const float A = fmaf(pa.z, r.e.z, fmaf(pa.y, r.e.y, pa.x * r.e.x));
+            const float wx = pa.x + r.k.x, wy = pa.y + r.k.y, wz = pa.z + r.k.z;
+            const float B = fmaf(hv, fmaf(wz, wz, fmaf(wy, wy, wx * wx)), r.k.w);
+            if (Q < r.b.w || B < b_tiny) {
+                const Pix64 px = a.p64[pt * TP + q];
+                if (px.g != 0.0) {
+                    double t64[kAcc];
+#pragma unroll
+                    for (int k = 0; k < kAcc; ++k) t64[k] = 0.0;
+                    const Seg64 s64 = a.s64[s];
+                    adj_pair64(px.n[0], px.n[1], px.n[2], px.g, s64, NG, t64, zerocnt);
+                    ++nearcnt;
+#pragma unroll
+                    for (int k = 0; k < kAcc; ++k) {
+                        const float th = __double2float_rn(t64[k]);
+                        fold(ahi[k], alo[k], th);
+                        alo[k] += __double2float_rn(t64[k] - (double)th);
+                    }
+                }
+            } else {
+                adj_pair32<NG9>(dx, dy, dz, Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) fold(ahi[k], alo[k], part[k]);
+    }
+}
+
+// One thread per sample.  Per stage the producer classifies the pixel tile against the CTA's
+// sample-tile cap and copies the pixel-pair far records (far tile) or the full Pix32 records.
+template <int NT, int TP, bool NG9>
+__global__ void __launch_bounds__(NT, 3) k_adj_f32c(AdjArgs a)
+{
+    constexpr size_t kStageBytes = TP * sizeof(Pix32);
+    static_assert(TP % 32 == 0 && (TP / 2) * sizeof(PixF2) <= kStageBytes, "stage layout");
     extern __shared__ __align__(128) unsigned char smem[];
-    Pix32 *sbuf = reinterpret_cast<Pix32 *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * TP * sizeof(Pix32));
+    unsigned char *sbuf = smem;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
     __shared__ int s_abort;
+    __shared__ int s_far[kStages];
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
@@ -183,16 +336,34 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
         const int nt = (int)(p1 - p0);
         const int64_t s = st * NT + tid;
         const Seg32 r = a.s32[s];
-        const float em1 = r.d.w - 1.f;   // Xdot.Xhat
-        const float hv = fmaf(-0.5f, r.k.w, 0.5f);
-        const SegCap sc = a.scaps[st];
         float ahi[kAcc], alo[kAcc];
 #pragma unroll
         for (int k = 0; k < kAcc; ++k) ahi[k] = alo[k] = 0.f;
 
+        auto issue = [&](int64_t pt, uint32_t gi) {
+            const int b = gi % kStages;
+            const SegCap sc = a.scaps[st];
+            const float4 pc = a.pcaps[pt];
+            const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
+            const float gap = sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w;
+            const float bx = pc.x - sc.b.x, by = pc.y - sc.b.y, bz = pc.z - sc.b.z;
+            const bool fast_b = sc.b.w < 0.f || sqrtf(bx * bx + by * by + bz * bz) > pc.w + sc.b.w;
+            const bool far = fast_b && (gap >= a.d_far);
+            s_far[b] = far;
+            unsigned char *dst = sbuf + (size_t)b * kStageBytes;
+            if (far) {
+                const uint32_t bytes = (uint32_t)((TP / 2) * sizeof(PixF2));
+                mbar_arrive_expect_tx(&bars[b], bytes);
+                bulk_g2s(dst, a.pf2 + pt * (TP / 2), bytes, &bars[b]);
+            } else {
+                const uint32_t bytes = (uint32_t)(TP * sizeof(Pix32));
+                mbar_arrive_expect_tx(&bars[b], bytes);
+                bulk_g2s(dst, a.p32 + pt * TP, bytes, &bars[b]);
+            }
+        };
         if (tid == 0) {
             const int pro = nt < kStages ? nt : kStages;
-            for (int i = 0; i < pro; ++i) issue_tile<Pix32, TP>(sbuf, bars, a.p32, p0 + i, gl + i);
+            for (int i = 0; i < pro; ++i) issue(p0 + i, gl + i);
         }
         int i = 0;
         for (; i < nt; ++i) {
@@ -201,74 +372,17 @@ __global__ void __launch_bounds__(NT, 2) k_adj_f32c(AdjArgs a)
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else {
-                const int64_t pt = p0 + i;
-                const float4 pc = a.pcaps[pt];
-                const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
-                const float gap = sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w;
-                const float bx = pc.x - sc.b.x, by = pc.y - sc.b.y, bz = pc.z - sc.b.z;
-                const bool fast_b = sc.b.w < 0.f || sqrtf(bx * bx + by * by + bz * bz) > pc.w + sc.b.w;
-                const bool far = fast_b && (gap >= a.d_far);
-                const Pix32 *sp = sbuf + buf * TP;
-                // FP32 partial sums over windows of 32 pixels, folded into compensated (hi, lo) pairs
-                for (int w0 = 0; w0 < TP; w0 += 32) {
-                    float part[kAcc];
-#pragma unroll
-                    for (int k = 0; k < kAcc; ++k) part[k] = 0.f;
-                    if (far) {
-                        // |d| >= d_far here: d from the leading floats is accurate to ~1e-7, and
-                        // Xdot.d = B - e, X'.d = A - f from the record's constants (their
-                        // cancellation costs at most a factor 1/|d| <= 4)
-#pragma unroll 2
-                        for (int q = w0; q < w0 + 32; ++q) {
-                            const float4 pa = sp[q].a;
-                            const float dx = pa.x - r.a.x, dy = pa.y - r.a.y, dz = pa.z - r.a.z;
-                            const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            const float A = fmaf(pa.z, r.e.z, fmaf(pa.y, r.e.y, pa.x * r.e.x));
-                            const float B = fmaf(pa.z, r.d.z, fmaf(pa.y, r.d.y, fmaf(pa.x, r.d.x, 1.f)));
-                            const float Pd = B - r.d.w, Qd = A - r.e.w;
-                            adj_pair32<NG9>(dx, dy, dz, Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
-                        }
-                    } else {
-                        const float b_tiny = a.b_min * 1e-3f;
-                        for (int q = w0; q < w0 + 32; ++q) {
-                            const float4 pa = sp[q].a, pb = sp[q].b;
-                            const float dx = (pa.x - r.a.x) + (pb.x - r.b.x);
-                            const float dy = (pa.y - r.a.y) + (pb.y - r.b.y);
-                            const float dz = (pa.z - r.a.z) + (pb.z - r.b.z);
-                            const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                            const float Pd = fmaf(r.d.z, dz, fmaf(r.d.y, dy, r.d.x * dx));
-                            const float Qd = fmaf(r.e.z, dz, fmaf(r.e.y, dy, r.e.x * dx));
-                            const float A = fmaf(pa.z, r.e.z, fmaf(pa.y, r.e.y, pa.x * r.e.x));
-                            const float wx = pa.x + r.k.x, wy = pa.y + r.k.y, wz = pa.z + r.k.z;
-                            const float B = fmaf(hv, fmaf(wz, wz, fmaf(wy, wy, wx * wx)), r.k.w);
-                            if (Q < r.b.w || B < b_tiny) {
-                                const Pix64 px = a.p64[pt * TP + q];
-                                if (px.g != 0.0) {
-                                    double t64[kAcc];
-#pragma unroll
-                                    for (int k = 0; k < kAcc; ++k) t64[k] = 0.0;
-                                    const Seg64 s64 = a.s64[s];
-                                    adj_pair64(px.n[0], px.n[1], px.n[2], px.g, s64, NG, t64, zerocnt);
-                                    ++nearcnt;
-#pragma unroll
-                                    for (int k = 0; k < kAcc; ++k) {
-                                        const float th = __double2float_rn(t64[k]);
-                                        fold(ahi[k], alo[k], th);
-                                        alo[k] += __double2float_rn(t64[k] - (double)th);
-                                    }
-                                }
-                            } else {
-                                adj_pair32<NG9>(dx, dy, dz, Q, A, B, Pd, Qd, em1, r.e.w, pa.w, pa.x, pa.y, pa.z, part);
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < kAcc; ++k) fold(ahi[k], alo[k], part[k]);
+                const unsigned char *stage = sbuf + (size_t)buf * kStageBytes;
+                if (s_far[buf]) {
+                    adj_far_stage<TP, NG9>(reinterpret_cast<const ulonglong2 *>(stage), r, ahi, alo);
+                } else {
+                    adj_checked_stage<TP, NG9>(reinterpret_cast<const Pix32 *>(stage), r, a, p0 + i, s, NG, ahi,
+                                               alo, nearcnt, zerocnt);
                 }
             }
             __syncthreads();
             if (s_abort) break;
-            if (tid == 0 && i + kStages < nt) issue_tile<Pix32, TP>(sbuf, bars, a.p32, p0 + i + kStages, gi + kStages);
+            if (tid == 0 && i + kStages < nt) issue(p0 + i + kStages, gi + kStages);
         }
         if (s_abort) {
             if (tid == 0) drain(bars, gl, i, i + kStages < nt ? i + kStages : nt, a.st);
@@ -410,12 +524,12 @@ int adj_slots(int prec, int ngrad, int num_sms)
 }
 
 void launch_pack_pixels(const double *nv, int64_t ldn, const int64_t *outidx, const double *g, int64_t tot,
-                        Pix32 *p32, Pix64 *p64, cudaStream_t s)
+                        Pix32 *p32, Pix64 *p64, PixF2 *pf2, cudaStream_t s)
 {
     int64_t blocks = (tot + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (blocks < 1) blocks = 1;
-    k_pack_pixels<<<(unsigned)blocks, 256, 0, s>>>(nv, ldn, outidx, g, tot, p32, p64);
+    k_pack_pixels<<<(unsigned)blocks, 256, 0, s>>>(nv, ldn, outidx, g, tot, p32, p64, pf2);
 }
 
 void launch_adjoint(int prec, const AdjArgs &a, int grid, cudaStream_t s)

@@ -15,7 +15,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsFlat, kWsClF, kWsAlm, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsFlat, kWsClF, kWsAlm, kWsPF2, kWsCount
 };
 static_assert(kWsCount <= kMaxWorkspaces, "isw_ctx holds kMaxWorkspaces workspace slots");
 
@@ -875,6 +875,7 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     if ((r = ensure_ws(c, kWsPcap, (size_t)pp.ntiles * sizeof(float4)))) return r;
     if ((r = ensure_ws(c, kWsP32, (size_t)pp.tot * sizeof(Pix32)))) return r;
     if ((r = ensure_ws(c, kWsP64, (size_t)pp.tot * sizeof(Pix64)))) return r;
+    if ((r = ensure_ws(c, kWsPF2, (size_t)(pp.tot / 2) * sizeof(PixF2)))) return r;
     if ((r = ensure_ws(c, kWsS32, (size_t)n_pad * sizeof(Seg32)))) return r;
     if ((r = ensure_ws(c, kWsS64, (size_t)n_pad * sizeof(Seg64)))) return r;
     if ((r = ensure_ws(c, kWsScap, (size_t)nseg_tiles * sizeof(SegCap)))) return r;
@@ -891,7 +892,8 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     SegCap *scaps = (SegCap *)c->ws[kWsScap];
     launch_pixel_table(nside, pp.mode, pix0, npix, pix_list, pp.tx, pp.ty, pp.ntiles, nv, pp.tot, outidx, pcaps,
                        c->d_status, s);
-    launch_pack_pixels(nv, pp.tot, outidx, dL_dtheta, pp.tot, p32, p64, s);
+    PixF2 *pf2 = (PixF2 *)c->ws[kWsPF2];
+    launch_pack_pixels(nv, pp.tot, outidx, dL_dtheta, pp.tot, p32, p64, pf2, s);
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, s32, s64, nullptr, c->d_status,
                 s);
     c->n_launch += 4;
@@ -902,6 +904,7 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     AdjArgs a;
     a.p32 = p32;
     a.p64 = p64;
+    a.pf2 = pf2;
     a.pcaps = pcaps;
     a.npix_tiles = pp.ntiles;
     a.s32 = s32;

@@ -414,6 +414,12 @@ struct __align__(16) Pix32 {
 struct __align__(16) Pix64 {
     double n[3], g;
 };
+// Far-field pixel records of the FP32 adjoint, one per pixel pair (pixels 2i, 2i+1 of the tile
+// order): a = (nx, nx', ny, ny'), b = (nz, nz', g, g') with the primed entries those of the second
+// pixel, so that each float pair is one packed f32x2 operand over the two pixels.
+struct __align__(16) PixF2 {
+    float4 a, b;
+};
 struct __align__(16) SegCap {
     float4 c;   // centre xyz, chord radius
     float4 r;   // rho_max, om_min, -, -

@@ -128,6 +128,7 @@ void launch_reduce_partials(const MapArgs &a, int tile_sz, cudaStream_t s);
 struct AdjArgs {
     const Pix32 *p32;        // pixel records in tile order
     const Pix64 *p64;
+    const PixF2 *pf2;        // far-field records of pixel pairs (FP32 kernel)
     const float4 *pcaps;     // pixel tile caps
     int64_t npix_tiles;
     const Seg32 *s32;
@@ -149,7 +150,7 @@ int adj_seg_tile(int prec);
 int adj_pix_tile(int prec);
 int adj_slots(int prec, int ngrad, int num_sms);
 void launch_pack_pixels(const double *nv, int64_t ldn, const int64_t *outidx, const double *g, int64_t tot,
-                        Pix32 *p32, Pix64 *p64, cudaStream_t s);
+                        Pix32 *p32, Pix64 *p64, PixF2 *pf2, cudaStream_t s);
 void launch_adjoint(int prec, const AdjArgs &a, int grid, cudaStream_t s);
 
 }  // namespace isw
