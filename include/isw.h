@@ -319,8 +319,9 @@ int isw_map_batched(isw_ctx *ctx, int64_t nside, const double *nodes, int64_t ld
  *   - Needs no isw_ctx and calls no cudaMalloc, cudaFree or allocating library routine.
  *     Its scratch is a static device array of 64 MiB that every GPU loading the library
  *     holds until the process exits; a problem whose scratch does not fit (roughly
- *     40 bytes per padded pixel + 270 bytes per padded sample, e.g. a full Nside=256 sky
- *     with 10^5 samples) is rejected with ISW_EINVAL before anything is enqueued.
+ *     32 bytes per padded pixel + 420 bytes per padded sample, plus 8 bytes per padded pixel
+ *     per segment chunk: a full Nside=256 sky fits with 8 x 10^4 samples, not with 10^5) is
+ *     rejected with ISW_EINVAL before anything is enqueued.
  *   - The first call on a device, with that device current, looks up the array's device
  *     address (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents; each call clears

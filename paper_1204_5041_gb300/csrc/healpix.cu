@@ -24,10 +24,31 @@ __global__ void k_pix2vec(int64_t N, int64_t pix0, int64_t npix, const int64_t *
     }
 }
 
+// Position (lx, ly) in a tx x ty block of the slot-th pixel when the block is enumerated by
+// anti-diagonals lx + ly from the largest down, lx ascending along each.  On a HEALPix base face
+// the ring number falls as ix + iy grows and the index within a ring grows with ix - iy, so this
+// order follows RING order: consecutive slots hold consecutive RING indices along each ring, and
+// the map kernels' per-slot stores of a warp land on a few contiguous runs of the output.
+__device__ __forceinline__ void diag_slot(int l, int tx, int ty, int &lx, int &ly)
+{
+    for (int s = tx + ty - 2; s >= 0; --s) {
+        const int lo = s - (ty - 1) > 0 ? s - (ty - 1) : 0, hi = s < tx - 1 ? s : tx - 1;
+        const int cnt = hi - lo + 1;
+        if (l < cnt) {
+            lx = lo + l;
+            ly = s - lx;
+            return;
+        }
+        l -= cnt;
+    }
+    lx = ly = 0;
+}
+
 // Pixel table in tile order.  Slot l of tile t holds the direction of one pixel and the
 // index its value is written to (RING index for full-sky maps, list position otherwise),
 // or -1 for padding.  Full-sky tiles are tx x ty blocks of face coordinates (compact
-// patches); range / list tiles are consecutive chunks of tx*ty pixels.
+// patches) with their slots in anti-diagonal (RING-following) order; range / list tiles are
+// consecutive chunks of tx*ty pixels.
 __global__ void k_pixel_table(int64_t N, int mode, int64_t pix0, int64_t npix, const int64_t *__restrict__ pix_list,
                               int tx, int ty, int64_t ntiles, double *__restrict__ nv, int64_t ldn,
                               int64_t *__restrict__ outidx, DevStatus *st)
@@ -44,7 +65,9 @@ __global__ void k_pixel_table(int64_t N, int mode, int64_t pix0, int64_t npix, c
             const int64_t f = t / (nbx * nby);
             const int64_t rem = t - f * nbx * nby;
             const int64_t by = rem / nbx, bx = rem - by * nbx;
-            const int64_t ix = bx * tx + (l % tx), iy = by * ty + (l / tx);
+            int lx, ly;
+            diag_slot(l, tx, ty, lx, ly);
+            const int64_t ix = bx * tx + lx, iy = by * ty + ly;
             if (ix < N && iy < N) {
                 ring = xyf2ring(N, (int)f, ix, iy);
                 oi = ring;

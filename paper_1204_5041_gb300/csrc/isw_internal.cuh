@@ -365,6 +365,13 @@ struct __align__(16) Far2 {
     float4 v[7];
 };
 constexpr int kFarConsts = 14;
+// Mid-range constants of one sample for the packed near-field loop, each value stored twice so
+// that one 8-byte load gives the (v, v) operand of an f32x2 instruction over two pixels:
+// Xhat hi (3), Xhat lo (3), Xdot (3), -X' (3), c, e = 1 + Xdot.Xhat, f = X'.Xhat, -f.
+struct __align__(16) Mid2 {
+    float4 v[8];
+};
+constexpr int kMidConsts = 16;
 
 // Packed FP32 pairs (f32x2, sm_100 and later): two IEEE single operations per instruction,
 // round to nearest; a 64-bit register holds (lo, hi).

@@ -78,11 +78,20 @@ void launch_cone_cut(const double *S, int64_t ld, int64_t n, const int64_t *off,
                      double xo2, int32_t *incl, int64_t *block_tot, double *out, int64_t ld_out, int64_t *off_out,
                      int64_t *count, cudaStream_t s);
 
+// sort.cu: spatial order of the samples (stable radix sort of the Morton code of Xhat); returns the
+// device array perm[n] (record s holds sample perm[s]), inside scratch of sort_scratch_bytes(n)
+size_t sort_scratch_bytes(int64_t n);
+const uint32_t *launch_spatial_order(const double *S, int64_t n, int64_t ld, double xo0, double xo1, double xo2,
+                                     void *scratch, cudaStream_t s);
+int spatial_order_launches();
+
 // pack.cu: per-sample records of the map kernels and per-tile caps
+// perm (may be NULL): record s is built from sample perm[s] (else from sample s)
 // far (may be NULL): far-field records for the FP32 pair kernel, pair-interleaved (n_pad even)
+// mid (may be NULL): mid-range records for the FP32 near-field pass
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
-                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, Far2 *far, DevStatus *st,
-                 cudaStream_t s);
+                 double theta_pix, double near_k, int64_t n_pad, const uint32_t *perm, Seg32 *s32, Seg64 *s64,
+                 Far2 *far, Mid2 *mid, DevStatus *st, cudaStream_t s);
 void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
                      SegCap *caps, cudaStream_t s);
 
@@ -96,6 +105,7 @@ struct MapArgs {
     const Seg32 *s32;
     const Seg64 *s64;
     const Far2 *far;         // far-field records of sample pairs (FP32 kernels)
+    const Mid2 *mid;         // mid-range records of samples (FP32 near-field pass)
     const SegCap *scaps;
     int64_t nst;             // segment tiles
     int split;               // segment chunks

@@ -160,13 +160,16 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
 // Near-field pass: per (pixel tile, segment chunk) item, the segment tiles that the far pass
 // skipped (class kMid or kChecked), found by a warp-wide scan of the tile classes; the result
 // is added to the chunk's partial (or to theta when there is one chunk) after the far pass.
-// Mid tiles use the float-pair form; checked tiles form B without cancellation and send pairs
-// with |d| < rho or B < b_min/1000 to FP64.
+// Pixels are held as pairs (pixels q and q + 1 of the thread) so that the mid-range loop runs in
+// packed f32x2 arithmetic over two pixels, reading each sample's constants from duplicated
+// (Mid2) records; checked tiles form B without cancellation and send pairs with |d| < rho or
+// B < b_min/1000 to FP64, one pixel at a time.
 template <int NT, int P, int S>
-__global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
+__global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near(MapArgs a)
 {
-    constexpr int TILE = NT * P;
-    constexpr size_t kStageBytes = S * sizeof(Seg32);
+    constexpr int TILE = NT * P, P2 = P / 2;
+    static_assert(P % 2 == 0, "pixels are held in pairs");
+    constexpr size_t kStageBytes = S * (sizeof(Mid2) > sizeof(Seg32) ? sizeof(Mid2) : sizeof(Seg32));
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sbuf = smem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
@@ -174,6 +177,7 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
     __shared__ int s_cls[kStages];
     __shared__ int64_t s_j[kStages];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t one2 = f2_pack(1.f, 1.f), half2 = f2_pack(0.5f, 0.5f);
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
@@ -189,26 +193,44 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
         const int64_t tile = item / a.split * a.tile_stride;
         const int kc = (int)(item % a.split);
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
-        float nh[P][3], nl[P][3], ahi[P], alo[P];
+        // pixel direction as a float pair (hi, lo), pixels 2pp and 2pp + 1 in the two halves
+        uint64_t nh2[P2][3], nl2[P2][3];
+        float ahi[P], alo[P];
         double a64[P];
         unsigned valid = 0;
 #pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
-            if (a.outidx[k] >= 0) valid |= 1u << q;
-            const double v[3] = {a.nv[k], a.nv[a.ldn + k], a.nv[2 * a.ldn + k]};
+        for (int pp = 0; pp < P2; ++pp) {
+            float h[2][3], l[2][3];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int q = 2 * pp + u;
+                const int64_t k = tile * TILE + (w * P + q) * 32 + lane;
+                if (a.outidx[k] >= 0) valid |= 1u << q;
+                const double v[3] = {a.nv[k], a.nv[a.ldn + k], a.nv[2 * a.ldn + k]};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    h[u][c] = __double2float_rn(v[c]);
+                    l[u][c] = __double2float_rn(v[c] - (double)h[u][c]);
+                }
+                ahi[q] = 0.f;
+                alo[q] = 0.f;
+                a64[q] = 0.0;
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                nh[q][c] = __double2float_rn(v[c]);
-                nl[q][c] = __double2float_rn(v[c] - (double)nh[q][c]);
+                nh2[pp][c] = f2_pack(h[0][c], h[1][c]);
+                nl2[pp][c] = f2_pack(l[0][c], l[1][c]);
             }
-            ahi[q] = 0.f;
-            alo[q] = 0.f;
-            a64[q] = 0.0;
         }
+        // the scalar (hi or lo) component c of pixel q
+        auto pix = [&](const uint64_t (&v)[P2][3], int q, int c) -> float {
+            float lo, hi;
+            f2_unpack(v[q >> 1][c], lo, hi);
+            return (q & 1) ? hi : lo;
+        };
         const float4 pc = a.pcaps[tile];
         // warp 0 finds the next segment tile of this chunk at or after `pos` that is not far;
-        // lane 0 issues it
+        // lane 0 issues it (Mid2 records for a mid tile, Seg32 records for a checked tile)
         int64_t pos = j0;
         auto issue_next = [&](uint32_t gi) {
             int64_t found = -1;
@@ -230,9 +252,12 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
                 const int b = gi % kStages;
                 s_j[b] = found;
                 s_cls[b] = cls;
-                if (found >= 0) {
-                    unsigned char *dst = sbuf + (size_t)b * kStageBytes;
-                    mbar_arrive_expect_tx(&bars[b], (uint32_t)kStageBytes);
+                unsigned char *dst = sbuf + (size_t)b * kStageBytes;
+                if (found >= 0 && cls == kMid) {
+                    mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Mid2)));
+                    bulk_g2s(dst, a.mid + found * S, (uint32_t)(S * sizeof(Mid2)), &bars[b]);
+                } else if (found >= 0) {
+                    mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Seg32)));
                     bulk_g2s(dst, a.s32 + found * S, (uint32_t)(S * sizeof(Seg32)), &bars[b]);
                 } else {
                     mbar_arrive_expect_tx(&bars[b], 0u);
@@ -253,54 +278,68 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
                 j = s_j[buf];
                 if (j >= 0) {
                     const int cls = s_cls[buf];
-                    const Seg32 *sb = reinterpret_cast<const Seg32 *>(sbuf + (size_t)buf * kStageBytes);
                     float part[P];
 #pragma unroll
                     for (int q = 0; q < P; ++q) part[q] = 0.f;
                     if (cls == kMid) {
-                        // per warp and sample: when every pair of the warp has 1 - n.Xhat >= d_far^2/2
+                        // Mid2 record: (Xh.x, Xh.y) (Xh.z, Xl.x) (Xl.y, Xl.z) (Xd.x, Xd.y) (Xd.z, -X'.x)
+                        // (-X'.y, -X'.z) (c, e) (f, -f), every entry a (v, v) pair.
+                        // Per warp and sample: when every pair of the warp has h = 1 - n.Xhat >= d_far^2/2
                         // (with a margin for its FP32 rounding), the direct far-field form
-                        // t = (c/2) [B (Xdot.d) - A (X'.d)] / [B (1 - n.Xhat)] with Xdot.d = B - e and
-                        // X'.d = A - f from the sample record; else the float-pair form in d
+                        // t = (c/2) [B (B - e) - A (A - f)] / [B h]; else d = n - Xhat as a float pair and
+                        // t = c [B Xdot.d - A X'.d] / [B d.d] with B = Xdot.d + e, A = X'.d + f.
+                        const ulonglong2 *mr = reinterpret_cast<const ulonglong2 *>(sbuf + (size_t)buf * kStageBytes);
                         const float hmin = 0.5f * a.d_far * a.d_far * 1.001f + 1e-6f;
+                        uint64_t part2[P2];
+#pragma unroll
+                        for (int pp = 0; pp < P2; ++pp) part2[pp] = 0ull;
                         for (int s = 0; s < S; ++s) {
-                            const float4 ra = sb[s].a;
-                            float h[P];
+                            const ulonglong2 r0 = mr[8 * s], r1 = mr[8 * s + 1];
+                            uint64_t h[P2];
                             bool ok = true;
 #pragma unroll
-                            for (int q = 0; q < P; ++q) {
-                                h[q] = fmaf(-nh[q][2], ra.z, fmaf(-nh[q][1], ra.y, fmaf(-nh[q][0], ra.x, 1.f)));
-                                ok = ok && (h[q] >= hmin);
+                            for (int pp = 0; pp < P2; ++pp) {
+                                h[pp] = f2_sub(one2, f2_fma(nh2[pp][2], r1.x, f2_fma(nh2[pp][1], r0.y, f2_mul(nh2[pp][0], r0.x))));
+                                float h0, h1;
+                                f2_unpack(h[pp], h0, h1);
+                                ok = ok && (h0 >= hmin) && (h1 >= hmin);
                             }
-                            const float4 rd = sb[s].d, re = sb[s].e;
+                            const ulonglong2 r3 = mr[8 * s + 3], r4 = mr[8 * s + 4], r5 = mr[8 * s + 5];
+                            const ulonglong2 r6 = mr[8 * s + 6], r7 = mr[8 * s + 7];
                             if (__all_sync(0xffffffffu, ok)) {
-                                const float ch = 0.5f * ra.w;
+                                const uint64_t ch = f2_mul(r6.x, half2);
 #pragma unroll
-                                for (int q = 0; q < P; ++q) {
-                                    const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
-                                    const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
-                                    const float num = fmaf(B, B - rd.w, -A * (A - re.w));
-                                    part[q] = fmaf(ch * num, rcp_approx(B * h[q]), part[q]);
+                                for (int pp = 0; pp < P2; ++pp) {
+                                    const uint64_t B = f2_fma(nh2[pp][2], r4.x, f2_fma(nh2[pp][1], r3.y, f2_fma(nh2[pp][0], r3.x, one2)));
+                                    const uint64_t An = f2_fma(nh2[pp][2], r5.y, f2_fma(nh2[pp][1], r5.x, f2_mul(nh2[pp][0], r4.y)));
+                                    const uint64_t num = f2_fma(An, f2_sub(r7.y, An), f2_mul(B, f2_sub(B, r6.y)));
+                                    float d0, d1;
+                                    f2_unpack(f2_mul(B, h[pp]), d0, d1);
+                                    part2[pp] = f2_fma(f2_mul(ch, num), f2_pack(rcp_approx(d0), rcp_approx(d1)), part2[pp]);
                                 }
                                 continue;
                             }
-                            const float4 rb = sb[s].b;
+                            const ulonglong2 r2 = mr[8 * s + 2];
 #pragma unroll
-                            for (int q = 0; q < P; ++q) {
-                                const float dx = (nh[q][0] - ra.x) + (nl[q][0] - rb.x);
-                                const float dy = (nh[q][1] - ra.y) + (nl[q][1] - rb.y);
-                                const float dz = (nh[q][2] - ra.z) + (nl[q][2] - rb.z);
-                                const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                                const float Pd = fmaf(rd.z, dz, fmaf(rd.y, dy, rd.x * dx));
-                                const float Qd = fmaf(re.z, dz, fmaf(re.y, dy, re.x * dx));
-                                const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
-                                const float B = fmaf(nh[q][2], rd.z, fmaf(nh[q][1], rd.y, fmaf(nh[q][0], rd.x, 1.f)));
-                                const float num = fmaf(B, Pd, -A * Qd);
-                                const float r = rcp_approx(B * Q);
-                                part[q] = fmaf(ra.w * num, r, part[q]);
+                            for (int pp = 0; pp < P2; ++pp) {
+                                const uint64_t dx = f2_add(f2_sub(nh2[pp][0], r0.x), f2_sub(nl2[pp][0], r1.y));
+                                const uint64_t dy = f2_add(f2_sub(nh2[pp][1], r0.y), f2_sub(nl2[pp][1], r2.x));
+                                const uint64_t dz = f2_add(f2_sub(nh2[pp][2], r1.x), f2_sub(nl2[pp][2], r2.y));
+                                const uint64_t Q = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                                const uint64_t Pd = f2_fma(r4.x, dz, f2_fma(r3.y, dy, f2_mul(r3.x, dx)));
+                                const uint64_t Qdn = f2_fma(r5.y, dz, f2_fma(r5.x, dy, f2_mul(r4.y, dx)));
+                                const uint64_t B = f2_add(Pd, r6.y);
+                                const uint64_t A = f2_sub(r7.x, Qdn);
+                                const uint64_t num = f2_fma(A, Qdn, f2_mul(B, Pd));
+                                float d0, d1;
+                                f2_unpack(f2_mul(B, Q), d0, d1);
+                                part2[pp] = f2_fma(f2_mul(r6.x, num), f2_pack(rcp_approx(d0), rcp_approx(d1)), part2[pp]);
                             }
                         }
+#pragma unroll
+                        for (int pp = 0; pp < P2; ++pp) f2_unpack(part2[pp], part[2 * pp], part[2 * pp + 1]);
                     } else {
+                        const Seg32 *sb = reinterpret_cast<const Seg32 *>(sbuf + (size_t)buf * kStageBytes);
                         const float b_tiny = a.b_min * 1e-3f;
                         for (int s = 0; s < S; ++s) {
                             const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e, rk = sb[s].k;
@@ -308,14 +347,15 @@ __global__ void __launch_bounds__(NT) k_map_f32c_near(MapArgs a)
                             unsigned mask = 0;
 #pragma unroll
                             for (int q = 0; q < P; ++q) {
-                                const float dx = (nh[q][0] - ra.x) + (nl[q][0] - rb.x);
-                                const float dy = (nh[q][1] - ra.y) + (nl[q][1] - rb.y);
-                                const float dz = (nh[q][2] - ra.z) + (nl[q][2] - rb.z);
+                                const float nx = pix(nh2, q, 0), ny = pix(nh2, q, 1), nz = pix(nh2, q, 2);
+                                const float dx = (nx - ra.x) + (pix(nl2, q, 0) - rb.x);
+                                const float dy = (ny - ra.y) + (pix(nl2, q, 1) - rb.y);
+                                const float dz = (nz - ra.z) + (pix(nl2, q, 2) - rb.z);
                                 const float Q = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                                 const float Pd = fmaf(rd.z, dz, fmaf(rd.y, dy, rd.x * dx));
                                 const float Qd = fmaf(re.z, dz, fmaf(re.y, dy, re.x * dx));
-                                const float A = fmaf(nh[q][2], re.z, fmaf(nh[q][1], re.y, nh[q][0] * re.x));
-                                const float wx = nh[q][0] + rk.x, wy = nh[q][1] + rk.y, wz = nh[q][2] + rk.z;
+                                const float A = fmaf(nz, re.z, fmaf(ny, re.y, nx * re.x));
+                                const float wx = nx + rk.x, wy = ny + rk.y, wz = nz + rk.z;
                                 const float B = fmaf(hv, fmaf(wz, wz, fmaf(wy, wy, wx * wx)), rk.w);
                                 if (Q < rb.w || B < b_tiny) {
                                     mask |= 1u << q;
@@ -530,7 +570,10 @@ void allow_smem(const void *fn, size_t bytes)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
-size_t smem_near(int S) { return kStages * S * sizeof(Seg32) + kStages * sizeof(uint64_t); }
+size_t smem_near(int S)
+{
+    return kStages * S * (sizeof(Mid2) > sizeof(Seg32) ? sizeof(Mid2) : sizeof(Seg32)) + kStages * sizeof(uint64_t);
+}
 size_t smem_f64(int S) { return kStages * S * sizeof(Seg64) + kStages * sizeof(uint64_t); }
 }  // namespace
 

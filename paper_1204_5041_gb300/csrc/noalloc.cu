@@ -6,8 +6,8 @@
 // synchronisation cudaMalloc and cudaFree may perform.  isw_map needs an isw_ctx, whose
 // creation and workspace growth allocate; this entry point needs neither.
 //
-// Its scratch (pixel table, sample records, far-field records, tile caps, segment-chunk partials and the
-// device status word) lives in one file-scope __device__ array of kStaticScratchBytes.
+// Its scratch (pixel table, spatial sort of the samples, sample records, far- and mid-range records, tile caps,
+// segment-chunk partials and the device status word) lives in one file-scope __device__ array of kStaticScratchBytes.
 // Every GPU that loads the library holds that array until the process exits.  All calls
 // share it and it keeps the previous call's contents: each call clears the status word and
 // overwrites every other byte it reads, and two calls that overlap on the GPU (different
@@ -123,6 +123,8 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     off[5] = at; at += up256((size_t)n_pad * sizeof(Seg64));
     off[6] = at; at += up256((size_t)nst * sizeof(SegCap));
     const size_t off_far = at; at += up256((size_t)(n_pad / 2) * sizeof(Far2));
+    const size_t off_mid = at; at += up256((size_t)n_pad * sizeof(Mid2));
+    const size_t off_sort = at; at += up256(sort_scratch_bytes(n));
     off[7] = at;
     if (at > kStaticScratchBytes) return ISW_EINVAL;  // problem too large for the static scratch
     // segment-chunk partials fit for at most `room` chunks
@@ -155,7 +157,9 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     const double theta_pix = std::sqrt(4.0 * M_PI / (12.0 * (double)nside * (double)nside));
     launch_pixel_table(nside, full ? 0 : 1, pix0, npix, nullptr, v.tx, v.ty, ntiles, nv, tot, outidx, pcaps, st, s);
     Far2 *far = (Far2 *)(b + off_far);
-    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, s32, s64, far, st, s);
+    const uint32_t *perm = launch_spatial_order(samples, n, ld, xo[0], xo[1], xo[2], b + off_sort, s);
+    Mid2 *mid = (Mid2 *)(b + off_mid);
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, perm, s32, s64, far, mid, st, s);
     launch_seg_caps(s32, s64, n, n_pad, S, 0.01f, scaps, s);
     MapArgs a;
     a.nv = nv;
@@ -166,6 +170,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.s32 = s32;
     a.s64 = s64;
     a.far = far;
+    a.mid = mid;
     a.scaps = scaps;
     a.nst = nst;
     a.split = split;

@@ -56,23 +56,25 @@ __device__ __forceinline__ void unit_dd(const double r[3], double hi[3], double 
 }
 
 __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, double xo0, double xo1, double xo2,
-                       double GU, double theta_pix, double near_k, int64_t n_pad, Seg32 *__restrict__ s32,
-                       Seg64 *__restrict__ s64, Far2 *__restrict__ far, DevStatus *ds)
+                       double GU, double theta_pix, double near_k, int64_t n_pad, const uint32_t *__restrict__ perm,
+                       Seg32 *__restrict__ s32, Seg64 *__restrict__ s64, Far2 *__restrict__ far,
+                       Mid2 *__restrict__ mid, DevStatus *ds)
 {
     unsigned long long bad = 0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
         Seg64 g;
         Seg32 f;
         if (s < n) {
-            const double r[3] = {dsub(S[s], xo0), dsub(S[ld + s], xo1), dsub(S[2 * ld + s], xo2)};
+            const int64_t src = perm ? (int64_t)perm[s] : s;   // record s holds sample perm[s]
+            const double r[3] = {dsub(S[src], xo0), dsub(S[ld + src], xo1), dsub(S[2 * ld + src], xo2)};
             double X;
             unit_dd(r, g.xh, g.xl, X);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                g.xd[k] = S[(3 + k) * ld + s];
-                g.xp[k] = S[(6 + k) * ld + s];
+                g.xd[k] = S[(3 + k) * ld + src];
+                g.xp[k] = S[(6 + k) * ld + src];
             }
-            const double dsig = S[9 * ld + s];
+            const double dsig = S[9 * ld + src];
             const double v2 = dadd(dadd(dmul(g.xd[0], g.xd[0]), dmul(g.xd[1], g.xd[1])), dmul(g.xd[2], g.xd[2]));
             const double xp2 = dadd(dadd(dmul(g.xp[0], g.xp[0]), dmul(g.xp[1], g.xp[1])), dmul(g.xp[2], g.xp[2]));
             const double om2 = dsub(1.0, v2);
@@ -140,6 +142,14 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
         }
         s32[s] = f;
         s64[s] = g;
+        if (mid) {
+            // from the FP32 record (a skipped or padding sample has c = 0: its terms are zero)
+            const float v[kMidConsts] = {f.a.x, f.a.y, f.a.z, f.b.x, f.b.y, f.b.z, f.d.x, f.d.y, f.d.z,
+                                         -f.e.x, -f.e.y, -f.e.z, f.a.w, f.d.w, f.e.w, -f.e.w};
+            float4 *dst = mid[s].v;
+#pragma unroll
+            for (int k = 0; k < kMidConsts / 2; ++k) dst[k] = make_float4(v[2 * k], v[2 * k], v[2 * k + 1], v[2 * k + 1]);
+        }
         if (far) {
             // far-field constants from the FP64 record (zero weight gives a zero record with sigma = 1)
             const double ch = 0.5 * g.c;
@@ -267,14 +277,14 @@ __global__ void k_seg_caps(const Seg32 *__restrict__ s32, const Seg64 *__restric
 }
 
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
-                 double theta_pix, double near_k, int64_t n_pad, Seg32 *s32, Seg64 *s64, Far2 *far, DevStatus *st,
-                 cudaStream_t s)
+                 double theta_pix, double near_k, int64_t n_pad, const uint32_t *perm, Seg32 *s32, Seg64 *s64,
+                 Far2 *far, Mid2 *mid, DevStatus *st, cudaStream_t s)
 {
     if (n_pad <= 0) return;
     int64_t blocks = (n_pad + 127) / 128;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_pack<<<(unsigned)blocks, 128, 0, s>>>(samples, n, ld, xo0, xo1, xo2, GU, theta_pix, near_k, n_pad, s32, s64,
-                                             far, st);
+    k_pack<<<(unsigned)blocks, 128, 0, s>>>(samples, n, ld, xo0, xo1, xo2, GU, theta_pix, near_k, n_pad, perm, s32,
+                                             s64, far, mid, st);
 }
 
 void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
