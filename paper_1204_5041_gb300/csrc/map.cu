@@ -160,16 +160,17 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
 // Near-field pass: per (pixel tile, segment chunk) item, the segment tiles that the far pass
 // skipped (class kMid or kChecked), found by a warp-wide scan of the tile classes; the result
 // is added to the chunk's partial (or to theta when there is one chunk) after the far pass.
-// Pixels are held as pairs (pixels q and q + 1 of the thread) so that the mid-range loop runs in
-// packed f32x2 arithmetic over two pixels, reading each sample's constants from duplicated
-// (Mid2) records; checked tiles form B without cancellation and send pairs with |d| < rho or
-// B < b_min/1000 to FP64, one pixel at a time.
+// Pixels are held as pairs (pixels q and q + 1 of the thread) so that the loops run in packed
+// f32x2 arithmetic over two pixels, reading each sample's constants from duplicated (Mid2)
+// records.  In checked tiles a sample whose warp has a pair within the near radius or with
+// B < b_min is redone one pixel at a time: B without cancellation, FP64 for pairs with
+// |d| < rho or B < b_min/1000.
 template <int NT, int P, int S>
 __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near(MapArgs a)
 {
     constexpr int TILE = NT * P, P2 = P / 2;
     static_assert(P % 2 == 0, "pixels are held in pairs");
-    constexpr size_t kStageBytes = S * (sizeof(Mid2) > sizeof(Seg32) ? sizeof(Mid2) : sizeof(Seg32));
+    constexpr size_t kStageBytes = S * sizeof(Mid2);
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sbuf = smem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
         };
         const float4 pc = a.pcaps[tile];
         // warp 0 finds the next segment tile of this chunk at or after `pos` that is not far;
-        // lane 0 issues it (Mid2 records for a mid tile, Seg32 records for a checked tile)
+        // lane 0 issues the copy of its Mid2 records
         int64_t pos = j0;
         auto issue_next = [&](uint32_t gi) {
             int64_t found = -1;
@@ -253,12 +254,9 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
                 s_j[b] = found;
                 s_cls[b] = cls;
                 unsigned char *dst = sbuf + (size_t)b * kStageBytes;
-                if (found >= 0 && cls == kMid) {
+                if (found >= 0) {
                     mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Mid2)));
                     bulk_g2s(dst, a.mid + found * S, (uint32_t)(S * sizeof(Mid2)), &bars[b]);
-                } else if (found >= 0) {
-                    mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Seg32)));
-                    bulk_g2s(dst, a.s32 + found * S, (uint32_t)(S * sizeof(Seg32)), &bars[b]);
                 } else {
                     mbar_arrive_expect_tx(&bars[b], 0u);
                 }
@@ -339,10 +337,47 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
 #pragma unroll
                         for (int pp = 0; pp < P2; ++pp) f2_unpack(part2[pp], part[2 * pp], part[2 * pp + 1]);
                     } else {
-                        const Seg32 *sb = reinterpret_cast<const Seg32 *>(sbuf + (size_t)buf * kStageBytes);
+                        // checked tile: per sample, the packed float-pair form for every pixel pair; kept
+                        // when no pair of the warp is within the tile's largest near radius and every
+                        // B is at least b_min (as in a mid tile), else the sample is redone one pixel at a
+                        // time from its Seg32 record: B without cancellation, FP64 for |d| < rho or
+                        // B < b_min / 1000
+                        const ulonglong2 *mr = reinterpret_cast<const ulonglong2 *>(sbuf + (size_t)buf * kStageBytes);
+                        const float rmax = a.scaps[j].r.x, rho2 = rmax * rmax, b_safe = a.b_min;
                         const float b_tiny = a.b_min * 1e-3f;
+                        uint64_t part2[P2];
+#pragma unroll
+                        for (int pp = 0; pp < P2; ++pp) part2[pp] = 0ull;
                         for (int s = 0; s < S; ++s) {
-                            const float4 ra = sb[s].a, rb = sb[s].b, rd = sb[s].d, re = sb[s].e, rk = sb[s].k;
+                            const ulonglong2 r0 = mr[8 * s], r1 = mr[8 * s + 1], r2 = mr[8 * s + 2], r3 = mr[8 * s + 3];
+                            const ulonglong2 r4 = mr[8 * s + 4], r5 = mr[8 * s + 5], r6 = mr[8 * s + 6], r7 = mr[8 * s + 7];
+                            uint64_t t2[P2];
+                            bool ok = true;
+#pragma unroll
+                            for (int pp = 0; pp < P2; ++pp) {
+                                const uint64_t dx = f2_add(f2_sub(nh2[pp][0], r0.x), f2_sub(nl2[pp][0], r1.y));
+                                const uint64_t dy = f2_add(f2_sub(nh2[pp][1], r0.y), f2_sub(nl2[pp][1], r2.x));
+                                const uint64_t dz = f2_add(f2_sub(nh2[pp][2], r1.x), f2_sub(nl2[pp][2], r2.y));
+                                const uint64_t Q = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+                                const uint64_t Pd = f2_fma(r4.x, dz, f2_fma(r3.y, dy, f2_mul(r3.x, dx)));
+                                const uint64_t Qdn = f2_fma(r5.y, dz, f2_fma(r5.x, dy, f2_mul(r4.y, dx)));
+                                const uint64_t B = f2_add(Pd, r6.y);
+                                const uint64_t A = f2_sub(r7.x, Qdn);
+                                const uint64_t num = f2_fma(A, Qdn, f2_mul(B, Pd));
+                                float q0, q1, b0, b1, d0, d1;
+                                f2_unpack(Q, q0, q1);
+                                f2_unpack(B, b0, b1);
+                                ok = ok && (q0 >= rho2) && (q1 >= rho2) && (b0 >= b_safe) && (b1 >= b_safe);
+                                f2_unpack(f2_mul(B, Q), d0, d1);
+                                t2[pp] = f2_mul(f2_mul(r6.x, num), f2_pack(rcp_approx(d0), rcp_approx(d1)));
+                            }
+                            if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+                                for (int pp = 0; pp < P2; ++pp) part2[pp] = f2_add(part2[pp], t2[pp]);
+                                continue;
+                            }
+                            const Seg32 rec = a.s32[j * S + s];
+                            const float4 ra = rec.a, rb = rec.b, rd = rec.d, re = rec.e, rk = rec.k;
                             const float hv = fmaf(-0.5f, rk.w, 0.5f);   // |Xdot| / 2
                             unsigned mask = 0;
 #pragma unroll
@@ -380,6 +415,13 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
                                     }
                                 }
                             }
+                        }
+#pragma unroll
+                        for (int pp = 0; pp < P2; ++pp) {
+                            float lo, hi;
+                            f2_unpack(part2[pp], lo, hi);
+                            part[2 * pp] += lo;
+                            part[2 * pp + 1] += hi;
                         }
                     }
 #pragma unroll
@@ -570,10 +612,7 @@ void allow_smem(const void *fn, size_t bytes)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
-size_t smem_near(int S)
-{
-    return kStages * S * (sizeof(Mid2) > sizeof(Seg32) ? sizeof(Mid2) : sizeof(Seg32)) + kStages * sizeof(uint64_t);
-}
+size_t smem_near(int S) { return kStages * S * sizeof(Mid2) + kStages * sizeof(uint64_t); }
 size_t smem_f64(int S) { return kStages * S * sizeof(Seg64) + kStages * sizeof(uint64_t); }
 }  // namespace
 
