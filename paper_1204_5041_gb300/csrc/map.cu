@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT, MINB) k_map_f32c(MapArgs a)
                 uint64_t part[P];
 #pragma unroll
                 for (int q = 0; q < P; ++q) part[q] = 0ull;   // (+0, +0)
-#pragma unroll 2
+#pragma unroll 1
                 for (int s = 0; s < S2; ++s) {
                     // (a.x, a.y) (a.z, a.w) (b.x, b.y) (b.z, b.w) (c.x, c.y) (c.z, c.w) (d.x, d.y),
                     // every entry a pair over the two samples
