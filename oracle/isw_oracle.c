@@ -125,11 +125,12 @@ void or_sincos_turns(double w, double *s, double *c)
 }
 
 /* ------------------------------------------------------------------------------------
- * 2. HEALPix RING pixel centres (Sec. II.D of the paper; geometry of Gorski et al. 2005).
+ * 2. HEALPix RING pixel centres (Sec. II.D of the paper; the pixel-centre relations of
+ * Gorski et al. 2005, Sec. 4).
  *
  * Rings are numbered 1..4N-1 from the north pole.  North polar cap: ring i < N holds 4i
- * pixels, z = 1 - i^2/(3N^2), phi = pi (2j-1)/(4i).  Equatorial belt N <= i <= 3N: 4N
- * pixels, z = 4/3 - 2i/(3N), phi = pi (2j - s)/(4N) with s = 2 when i + N is odd and
+ * pixels, z = 1 - i^2/(3N^2), phi = (pi/(2i)) (j - 1/2).  Equatorial belt N <= i <= 3N: 4N
+ * pixels, z = 4/3 - 2i/(3N), phi = (pi/(2N)) (j - s/2) with s = 2 when i + N is odd and
  * s = 1 when it is even (rings alternate between a pixel centred on phi = 0 and a half-pixel
  * offset; the first pixel of a ring is the one at or just after phi = 0).  South cap
  * mirrors the north.  z and sin(theta) are formed from exact integers with one division:
@@ -827,13 +828,17 @@ int or_lightcone_adjoint(int mode, const double *nodes, int64_t n, int64_t ld,
  *     atan(a) = 2 atan(a / (1 + sqrt(1 + a^2))) leaves |v| <= 0.2; atan(v) by its Taylor
  *     series v (1 - v^2/3 + v^4/5 - ...), 13 terms summed from the smallest; the octant is
  *     unfolded exactly.  Pinned against mpmath (<= 4 ulp).
- * (b) RING vec2pix: the published HEALPix assignment (Gorski et al. 2005): z = cos(theta),
- *     t = phi / (pi/2) in [0, 4); equatorial belt |z| <= 2/3: the pixel's two edge-line
- *     indices jp = floor(N (1/2 + t - 3z/4)), jm = floor(N (1/2 + t + 3z/4)) give the ring
- *     and the position in it; polar caps: with tp = frac(t) and h = N sqrt(3 (1 - |z|)),
- *     jp = floor(tp h), jm = floor((1 - tp) h), ring jp + jm + 1 counted from the pole and
- *     position floor(t * ring).  Pinned by vec2pix(pix2vec(p)) = p, by an independent numpy
- *     statement of the same rules away from pixel edges, and by equal-area counts.
+ * (b) RING vec2pix, from the pixel-boundary curves of Gorski et al. (2005, Sec. 4): with
+ *     z = cos(theta), t = phi / (pi/2) in [0, 4), the equatorial-zone boundaries are the lines
+ *     z = 2/3 - 4k/(3N) +- 8 phi/(3 pi) and the polar-cap boundaries the curves
+ *     z = 1 - (k/N)^2 (pi/(2 phi_t))^2 / 3 and z = 1 - (k/N)^2 (pi/(2 phi_t - pi))^2 / 3,
+ *     phi_t = phi mod pi/2.  Solving each family for k at the direction counts the curves below
+ *     it: in the belt |z| <= 2/3, jp = floor(N (1/2 + t - 3z/4)), jm = floor(N (1/2 + t + 3z/4)),
+ *     ring N + 1 + jp - jm and position (jp + jm - N + kshift + 1)/2; in a cap, with
+ *     tp = frac(t) and h = N sqrt(3 (1 - |z|)), jp = floor(tp h), jm = floor((1 - tp) h), ring
+ *     jp + jm + 1 counted from the pole and position floor(t * ring).  Pinned by
+ *     vec2pix(pix2vec(p)) = p, by an independent numpy statement of the same rules away from
+ *     pixel edges, and by equal-area counts.
  * (c) box placement: shell k takes the nodes of box b_k and maps X -> R X + T, Xdot -> R Xdot,
  *     X' -> R X' (R row-major, (R x)_i = (R_i0 x_0 + R_i1 x_1) + R_i2 x_2), dsigma unchanged.
  * (d) cone cut: a light-cone sample of shell k is kept when the direction of X - x_obs lies

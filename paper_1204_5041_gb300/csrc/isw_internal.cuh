@@ -106,10 +106,10 @@ __device__ __forceinline__ int64_t isqrt64(int64_t v)
     return r;
 }
 
-// Centre of RING pixel p at resolution N (HEALPix geometry, Gorski et al. 2005): rings
-// i = 1..4N-1 from the north; polar caps hold 4i pixels at z = +-(1 - i^2/(3N^2)),
-// phi = pi (2j-1)/(4i); the belt holds 4N pixels at z = (4N - 2i)/(3N),
-// phi = pi (2j - s)/(4N), s = 2 when i + N is odd, 1 when even.
+// Centre of RING pixel p at resolution N (the pixel-centre relations of Gorski et al. 2005,
+// Sec. 4): rings i = 1..4N-1 from the north; the polar caps hold 4i pixels at
+// z = +-(1 - i^2/(3N^2)), phi = (pi/(2i)) (j - 1/2); the belt holds 4N pixels at
+// z = 4/3 - 2i/(3N), phi = (pi/(2N)) (j - s/2), s = 2 when i + N is odd, 1 when even.
 __device__ __forceinline__ void pix2vec_ring(int64_t N, int64_t p, double &x, double &y, double &z)
 {
     const int64_t npix = 12 * N * N;
@@ -180,10 +180,15 @@ __device__ __forceinline__ double atan2_quarter(double y, double x)
     return q;
 }
 
-// RING pixel of direction v (not necessarily unit, not zero): the published HEALPix rules with
-// z = cos(theta) and t = phi/(pi/2): equatorial belt |z| <= 2/3 from the two edge-line indices
-// floor(N (1/2 + t -+ 3z/4)), polar caps from floor(frac(t) h), floor((1 - frac(t)) h) with
-// h = N sqrt(3 (1 - |z|)) and the position floor(t * ring).
+// RING pixel of direction v (not necessarily unit, not zero), with z = cos(theta) and
+// t = phi/(pi/2) in [0, 4).  The pixel boundaries of Gorski et al. (2005, Sec. 4) are two
+// families of curves: in the equatorial zone the lines z = 2/3 - 4k/(3N) +- 8 phi/(3 pi), in
+// the polar caps z = 1 - (k/N)^2 (pi/(2 phi_t))^2 / 3 and z = 1 - (k/N)^2 (pi/(2 phi_t - pi))^2 / 3
+// with phi_t = phi mod pi/2.  Solved for k at the direction, each family gives how many of its
+// curves lie below it: jp = floor(N (1/2 + t - 3z/4)), jm = floor(N (1/2 + t + 3z/4)) in the
+// belt, jp = floor(t_p h), jm = floor((1 - t_p) h) with t_p = frac(t), h = N sqrt(3 (1 - |z|))
+// in a cap.  The ring is then N + 1 + jp - jm (belt) or jp + jm + 1 (counted from the nearer
+// pole), and the position in it (jp + jm - N + kshift + 1)/2 or floor(t * ring).
 __device__ __forceinline__ int64_t vec2pix_ring(int64_t N, double vx, double vy, double vz)
 {
     const double r = dsqrt(dadd(dadd(dmul(vx, vx), dmul(vy, vy)), dmul(vz, vz)));
@@ -213,10 +218,13 @@ __device__ __forceinline__ int64_t vec2pix_ring(int64_t N, double vx, double vy,
     return 12 * N * N - 2 * ir * (ir + 1) + ip;
 }
 
-// RING index of the pixel at (ix, iy) of base face f (0..11): the twelve base pixels are
-// rhombi; face f spans rings around jr(f)*N, with jr = 2 (north faces 0-3), 3 (equatorial
-// faces 4-7), 4 (south faces 8-11), and its corner sits at longitude jp(f) * pi/4.
-// Used only to order pixels in compact 2-D tiles; any bijection gives the same map.
+// RING index of the pixel at (ix, iy) of base face f (0..11).  The twelve base pixels of
+// Gorski et al. (2005, Sec. 4) are rhombi in three rings of four: face f is centred on ring
+// jr(f) * N, jr = 2 (north faces 0-3), 3 (equatorial faces 4-7), 4 (south faces 8-11), with its
+// corner at longitude jp(f) * pi/4; inside a face, ring number falls by one per step of ix + iy
+// and the position in the ring rises by one per two steps of ix - iy (plus the half-pixel
+// shift kshift of alternate belt rings).  Used only to order pixels in compact 2-D tiles; any
+// bijection gives the same map.
 __device__ __forceinline__ int64_t xyf2ring(int64_t N, int f, int64_t ix, int64_t iy)
 {
     const int jr_face = (f < 4) ? 2 : (f < 8 ? 3 : 4);
