@@ -15,7 +15,7 @@ namespace {
 
 enum WsSlot {
     kWsNv = 0, kWsOut, kWsPcap, kWsS32, kWsS64, kWsScap, kWsPartial, kWsMisc,
-    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsFlat, kWsClF, kWsAlm, kWsPF2, kWsSort, kWsMid, kWsCount
+    kWsP32, kWsP64, kWsAdjPartial, kWsSamples, kWsShell, kWsFar, kWsLoops, kWsQueue, kWsConeMeta, kWsCut, kWsFlat, kWsClF, kWsAlm, kWsPF2, kWsSort, kWsMid, kWsFar64, kWsCount
 };
 static_assert(kWsCount <= kMaxWorkspaces, "isw_ctx holds kMaxWorkspaces workspace slots");
 
@@ -228,6 +228,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     if ((r = ensure_ws(c, kWsScap, (size_t)nst * sizeof(SegCap)))) return r;
     if (prec == ISW_F32C && (r = ensure_ws(c, kWsFar, (size_t)(n_pad / 2) * sizeof(Far2)))) return r;
     if (prec == ISW_F32C && (r = ensure_ws(c, kWsMid, (size_t)n_pad * sizeof(Mid2)))) return r;
+    if (prec == ISW_F64 && (r = ensure_ws(c, kWsFar64, (size_t)n_pad * sizeof(Far64)))) return r;
     if (split > 1 && (r = ensure_ws(c, kWsPartial, (size_t)split * pp.tot * sizeof(double)))) return r;
     if ((r = ensure_ws(c, kWsQueue, 2 * sizeof(unsigned long long)))) return r;
     if (prec == ISW_F32C && (r = ensure_ws(c, kWsSort, sort_scratch_bytes(n)))) return r;
@@ -246,6 +247,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
                             pcaps, c->d_status, s);
     Far2 *far = prec == ISW_F32C ? (Far2 *)c->ws[kWsFar] : nullptr;
     Mid2 *mid = prec == ISW_F32C ? (Mid2 *)c->ws[kWsMid] : nullptr;
+    Far64 *far64 = prec == ISW_F64 ? (Far64 *)c->ws[kWsFar64] : nullptr;
     // FP32 path: records in the spatial order of the samples (tight segment-tile caps)
     const uint32_t *perm = nullptr;
     if (prec == ISW_F32C) {
@@ -253,12 +255,9 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
         c->n_launch += spatial_order_launches();
     }
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, perm, s32, s64, far, mid,
-                c->d_status, s);
-    c->n_launch += 3;
-    if (prec == ISW_F32C) {
-        launch_seg_caps(s32, s64, n, n_pad, S, (float)c->b_min, scaps, s);
-        c->n_launch += 1;
-    }
+                far64, c->d_status, s);
+    launch_seg_caps(s32, s64, n, n_pad, S, (float)c->b_min, scaps, s);
+    c->n_launch += 4;
 
     MapArgs a;
     a.nv = nv;
@@ -270,6 +269,7 @@ int map_impl(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const int64_
     a.s64 = s64;
     a.far = far;
     a.mid = mid;
+    a.far64 = far64;
     a.scaps = scaps;
     a.nst = nst;
     a.split = split;
@@ -906,7 +906,7 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     PixF2 *pf2 = (PixF2 *)c->ws[kWsPF2];
     launch_pack_pixels(nv, pp.tot, outidx, dL_dtheta, pp.tot, p32, p64, pf2, s);
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, nullptr, s32, s64, nullptr,
-                nullptr, c->d_status, s);
+                nullptr, nullptr, c->d_status, s);
     c->n_launch += 4;
     if (prec == ISW_F32C) {
         launch_seg_caps(s32, s64, n, n_pad, NT, (float)c->b_min, scaps, s);

@@ -89,9 +89,10 @@ int spatial_order_launches();
 // perm (may be NULL): record s is built from sample perm[s] (else from sample s)
 // far (may be NULL): far-field records for the FP32 pair kernel, pair-interleaved (n_pad even)
 // mid (may be NULL): mid-range records for the FP32 near-field pass
+// far64 (may be NULL): far-field records for the FP64 kernel
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
                  double theta_pix, double near_k, int64_t n_pad, const uint32_t *perm, Seg32 *s32, Seg64 *s64,
-                 Far2 *far, Mid2 *mid, DevStatus *st, cudaStream_t s);
+                 Far2 *far, Mid2 *mid, Far64 *far64, DevStatus *st, cudaStream_t s);
 void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
                      SegCap *caps, cudaStream_t s);
 
@@ -106,6 +107,7 @@ struct MapArgs {
     const Seg64 *s64;
     const Far2 *far;         // far-field records of sample pairs (FP32 kernels)
     const Mid2 *mid;         // mid-range records of samples (FP32 near-field pass)
+    const Far64 *far64;      // far-field records of samples (FP64 kernel)
     const SegCap *scaps;
     int64_t nst;             // segment tiles
     int split;               // segment chunks

@@ -471,15 +471,34 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
     }
 }
 
-// Plain FP64 path: every pair in FP64, same tiling.
+// 1/x for a positive normal double within the float range: the FP32 hardware estimate refined by
+// two Newton steps (relative error ~2^-22 -> 2^-44 -> below an ulp), five FP64 operations
+// instead of the IEEE division's longer sequence.
+__device__ __forceinline__ double rcp64(double x)
+{
+    double r = (double)rcp_approx((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+// Plain FP64 path: every pair in FP64, same tiling.  Segment tiles whose cap is at least d_far
+// from the pixel tile's cap are evaluated in the FP64 far-field form
+// t = (c/2) [B (B - e) - A (A - f)] / [B (1 - n.Xhat)] (Far64 records: the cancellation in
+// 1 - n.Xhat costs at most a factor 2/d_far^2 = 32 of the 1e-16 rounding); the others pair by
+// pair from d = n - Xhat formed from the double-double Xhat, with the IEEE division.
 template <int NT, int P, int S>
 __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
 {
     constexpr int TILE = NT * P;
+    constexpr size_t kStageBytes = S * sizeof(Seg64);
+    static_assert(sizeof(Far64) <= sizeof(Seg64), "stage layout");
     extern __shared__ __align__(128) unsigned char smem[];
-    Seg64 *sbuf = reinterpret_cast<Seg64 *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * S * sizeof(Seg64));
+    unsigned char *sbuf = smem;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
     __shared__ int s_abort;
+    __shared__ int s_far[kStages];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         for (int b = 0; b < kStages; ++b) mbar_init(&bars[b], 1);
@@ -509,9 +528,25 @@ __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
             hi[q] = 0.0;
             lo[q] = 0.0;
         }
+        const float4 pc = a.pcaps[tile];
+        auto issue = [&](int64_t j, uint32_t gi) {
+            const int b = gi % kStages;
+            const SegCap sc = a.scaps[j];
+            const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
+            const bool far = sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w >= a.d_far;
+            s_far[b] = far;
+            unsigned char *dst = sbuf + (size_t)b * kStageBytes;
+            if (far) {
+                mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Far64)));
+                bulk_g2s(dst, a.far64 + j * S, (uint32_t)(S * sizeof(Far64)), &bars[b]);
+            } else {
+                mbar_arrive_expect_tx(&bars[b], (uint32_t)(S * sizeof(Seg64)));
+                bulk_g2s(dst, a.s64 + j * S, (uint32_t)(S * sizeof(Seg64)), &bars[b]);
+            }
+        };
         if (tid == 0) {
             const int pro = nt < kStages ? nt : kStages;
-            for (int i = 0; i < pro; ++i) issue_tile<Seg64, S>(sbuf, bars, a.s64, j0 + i, g + i);
+            for (int i = 0; i < pro; ++i) issue(j0 + i, g + i);
         }
         int i = 0;
         for (; i < nt; ++i) {
@@ -520,27 +555,42 @@ __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bars[buf], (gi / kStages) & 1, a.wait_polls))) {
                 s_abort = 1;
             } else {
-                const Seg64 *sb = sbuf + buf * S;
                 double part[P];
 #pragma unroll
                 for (int q = 0; q < P; ++q) part[q] = 0.0;
-                unsigned z[P];
+                if (s_far[buf]) {
+                    const Far64 *fb = reinterpret_cast<const Far64 *>(sbuf + (size_t)buf * kStageBytes);
+                    for (int s = 0; s < S; ++s) {
+                        const Far64 r = fb[s];
 #pragma unroll
-                for (int q = 0; q < P; ++q) z[q] = 0;
-                for (int s = 0; s < S; ++s) {
-                    const Seg64 g64 = sb[s];
+                        for (int q = 0; q < P; ++q) {
+                            const double h1 = fma(nv[q][2], r.mxh[2], fma(nv[q][1], r.mxh[1], fma(nv[q][0], r.mxh[0], 1.0)));
+                            const double B = fma(nv[q][2], r.xd[2], fma(nv[q][1], r.xd[1], fma(nv[q][0], r.xd[0], 1.0)));
+                            const double A = fma(nv[q][2], r.xp[2], fma(nv[q][1], r.xp[1], nv[q][0] * r.xp[0]));
+                            const double num = fma(B, B - r.e, -(A * (A - r.f)));
+                            part[q] = fma(r.ch * num, rcp64(B * h1), part[q]);
+                        }
+                    }
+                } else {
+                    const Seg64 *sb = reinterpret_cast<const Seg64 *>(sbuf + (size_t)buf * kStageBytes);
+                    unsigned z[P];
 #pragma unroll
-                    for (int q = 0; q < P; ++q) part[q] += pair64(nv[q][0], nv[q][1], nv[q][2], g64, z[q]);
+                    for (int q = 0; q < P; ++q) z[q] = 0;
+                    for (int s = 0; s < S; ++s) {
+                        const Seg64 g64 = sb[s];
+#pragma unroll
+                        for (int q = 0; q < P; ++q) part[q] += pair64(nv[q][0], nv[q][1], nv[q][2], g64, z[q]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < P; ++q)
+                        if (valid & (1u << q)) zerocnt += z[q];
                 }
-#pragma unroll
-                for (int q = 0; q < P; ++q)
-                    if (valid & (1u << q)) zerocnt += z[q];
 #pragma unroll
                 for (int q = 0; q < P; ++q) fold64(hi[q], lo[q], part[q]);
             }
             __syncthreads();
             if (s_abort) break;
-            if (tid == 0 && i + kStages < nt) issue_tile<Seg64, S>(sbuf, bars, a.s64, j0 + i + kStages, gi + kStages);
+            if (tid == 0 && i + kStages < nt) issue(j0 + i + kStages, gi + kStages);
         }
         if (s_abort) {
             if (tid == 0) drain(bars, g, i, i + kStages < nt ? i + kStages : nt, a.st);

@@ -159,7 +159,8 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     Far2 *far = (Far2 *)(b + off_far);
     const uint32_t *perm = launch_spatial_order(samples, n, ld, xo[0], xo[1], xo[2], b + off_sort, s);
     Mid2 *mid = (Mid2 *)(b + off_mid);
-    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, perm, s32, s64, far, mid, st, s);
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, perm, s32, s64, far, mid, nullptr, st,
+                s);
     launch_seg_caps(s32, s64, n, n_pad, S, 0.01f, scaps, s);
     MapArgs a;
     a.nv = nv;
@@ -171,6 +172,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.s64 = s64;
     a.far = far;
     a.mid = mid;
+    a.far64 = nullptr;
     a.scaps = scaps;
     a.nst = nst;
     a.split = split;

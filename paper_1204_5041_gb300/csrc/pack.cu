@@ -58,7 +58,7 @@ __device__ __forceinline__ void unit_dd(const double r[3], double hi[3], double 
 __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, double xo0, double xo1, double xo2,
                        double GU, double theta_pix, double near_k, int64_t n_pad, const uint32_t *__restrict__ perm,
                        Seg32 *__restrict__ s32, Seg64 *__restrict__ s64, Far2 *__restrict__ far,
-                       Mid2 *__restrict__ mid, DevStatus *ds)
+                       Mid2 *__restrict__ mid, Far64 *__restrict__ far64, DevStatus *ds)
 {
     unsigned long long bad = 0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n_pad; s += (int64_t)gridDim.x * blockDim.x) {
@@ -149,6 +149,19 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
             float4 *dst = mid[s].v;
 #pragma unroll
             for (int k = 0; k < kMidConsts / 2; ++k) dst[k] = make_float4(v[2 * k], v[2 * k], v[2 * k + 1], v[2 * k + 1]);
+        }
+        if (far64) {
+            Far64 r;
+            const double xh[3] = {g.xh[0] + g.xl[0], g.xh[1] + g.xl[1], g.xh[2] + g.xl[2]};
+            for (int k = 0; k < 3; ++k) {
+                r.mxh[k] = -xh[k];
+                r.xd[k] = g.xd[k];
+                r.xp[k] = g.xp[k];
+            }
+            r.ch = 0.5 * g.c;
+            r.e = 1.0 + (g.xd[0] * xh[0] + g.xd[1] * xh[1] + g.xd[2] * xh[2]);
+            r.f = g.xp[0] * xh[0] + g.xp[1] * xh[1] + g.xp[2] * xh[2];
+            far64[s] = r;
         }
         if (far) {
             // far-field constants from the FP64 record (zero weight gives a zero record with sigma = 1)
@@ -278,13 +291,13 @@ __global__ void k_seg_caps(const Seg32 *__restrict__ s32, const Seg64 *__restric
 
 void launch_pack(const double *samples, int64_t n, int64_t ld, double xo0, double xo1, double xo2, double GU,
                  double theta_pix, double near_k, int64_t n_pad, const uint32_t *perm, Seg32 *s32, Seg64 *s64,
-                 Far2 *far, Mid2 *mid, DevStatus *st, cudaStream_t s)
+                 Far2 *far, Mid2 *mid, Far64 *far64, DevStatus *st, cudaStream_t s)
 {
     if (n_pad <= 0) return;
     int64_t blocks = (n_pad + 127) / 128;
     if (blocks > 152 * 32) blocks = 152 * 32;
     k_pack<<<(unsigned)blocks, 128, 0, s>>>(samples, n, ld, xo0, xo1, xo2, GU, theta_pix, near_k, n_pad, perm, s32,
-                                             s64, far, mid, st);
+                                             s64, far, mid, far64, st);
 }
 
 void launch_seg_caps(const Seg32 *s32, const Seg64 *s64, int64_t n, int64_t n_pad, int seg_tile, float b_min,
