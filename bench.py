@@ -549,6 +549,7 @@ def run_case(args):
       adjoint_f32c  the FP32-compensated adjoint of synth.config(3) (50,176 samples) at Nside 128
       adjoint_f64   the FP64 adjoint of the same
       map_f32c      the FP32-compensated map of synth.config(1) (200,000 samples) at Nside 128
+                    (kernel variant --variant, default the library's first)
     Each runs --warmup untimed calls and then --steps timed ones."""
     import torch
 
@@ -561,6 +562,7 @@ def run_case(args):
     ctx = isw.default_context(0)
     if args.d_far is not None:
         ctx.set_param(isw.PARAM_D_FAR, args.d_far)
+    ctx.set_param(isw.PARAM_VARIANT, args.variant)
     nodes = torch.from_numpy(np.ascontiguousarray(w.nodes)).to(dev)
     loops = torch.from_numpy(np.ascontiguousarray(w.loop_params)).to(dev)
     samples = isw.lightcone_intersect_shells(nodes, w.shell_off, w.t_box, w.mode, loops, x_obs=w.x_obs,

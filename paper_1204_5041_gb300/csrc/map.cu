@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
     __shared__ int s_abort;
     __shared__ int s_cls[kStages];
     __shared__ int64_t s_j[kStages];
+    __shared__ int64_t s_first;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t one2 = f2_pack(1.f, 1.f), half2 = f2_pack(0.5f, 0.5f);
     if (tid == 0) {
@@ -194,6 +195,22 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
         const int64_t tile = item / a.split * a.tile_stride;
         const int kc = (int)(item % a.split);
         const int64_t j0 = a.nst * kc / a.split, j1 = a.nst * (kc + 1) / a.split;
+        const float4 pc = a.pcaps[tile];
+        // warp 0 finds the chunk's first segment tile that is not far; an item without one is
+        // skipped before its pixels are loaded (most items: strings cover little of the sky)
+        if (w == 0) {
+            int64_t first = -1;
+            for (int64_t p0 = j0; p0 < j1 && first < 0; p0 += 32) {
+                const int64_t jj = p0 + lane;
+                const int c = jj < j1 ? classify(pc, a.scaps[jj], a.d_far) : kFar;
+                const unsigned m = __ballot_sync(0xffffffffu, c != kFar);
+                if (m) first = p0 + __ffs(m) - 1;
+            }
+            if (lane == 0) s_first = first;
+        }
+        __syncthreads();
+        const int64_t first = s_first;
+        if (first < 0) continue;   // next_item's barriers order the next write of s_first
         // pixel direction as a float pair (hi, lo), pixels 2pp and 2pp + 1 in the two halves
         uint64_t nh2[P2][3], nl2[P2][3];
         float ahi[P], alo[P];
@@ -229,10 +246,9 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
             f2_unpack(v[q >> 1][c], lo, hi);
             return (q & 1) ? hi : lo;
         };
-        const float4 pc = a.pcaps[tile];
         // warp 0 finds the next segment tile of this chunk at or after `pos` that is not far;
         // lane 0 issues the copy of its Mid2 records
-        int64_t pos = j0;
+        int64_t pos = first;
         auto issue_next = [&](uint32_t gi) {
             int64_t found = -1;
             int cls = kFar;
