@@ -168,8 +168,8 @@ def profiled_traffic(variant: int):
 
 
 def profiled_fma_busy(variant: int):
-    """FMA-pipe busy fraction of the far-field pass (ncu capture of the bench workload)."""
-    v = _profile_record("pair_kernel_far_nside512.md", r"fma_pipe_busy=([0-9.]+)", variant)
+    """FMA-pipe busy fraction of the far-field pass (ncu capture of the bench's samples on a smaller sky)."""
+    v = _profile_record("pair_kernel_far_nside128_200k_seg.md", r"fma_pipe_busy=([0-9.]+)", variant)
     return float(v) if v is not None else None
 
 
