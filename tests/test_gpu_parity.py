@@ -165,6 +165,28 @@ def test_map_deterministic(isw, cfg0):
         assert np.array_equal(a.view(np.int64), b.view(np.int64))
 
 
+def test_map_independent_of_sample_order(isw):
+    """The FP32 path writes its records in a spatial (Morton) order of the samples: a permuted
+    input gives the same map up to the rounding of the different summation order, and both match
+    the oracle.  Also a ragged sample count (not a multiple of the sort's 1024-element blocks)."""
+    w = synth.config(1, seed=4)
+    S, _, st = oracle.lightcone_workload(w)
+    assert np.all(st == 0)
+    S = np.ascontiguousarray(S[:, :150001])
+    perm = np.random.default_rng(9).permutation(S.shape[1])
+    nside = 128
+    a = isw.isw_map(nside, _d(S), prec="f32c").cpu().numpy()
+    b = isw.isw_map(nside, _d(np.ascontiguousarray(S[:, perm])), prec="f32c").cpu().numpy()
+    assert _status_ok(isw)[0] == isw.OK
+    pix = np.random.default_rng(10).choice(a.size, 2000, replace=False)
+    ref, _ = oracle.isw_map(nside, S, pix=pix, threads=THREADS)
+    rms = np.sqrt(np.mean(ref ** 2))
+    d_ab = np.max(np.abs(a - b)) / np.sqrt(np.mean(a ** 2))
+    print(f"order: max|a - b|/rms = {d_ab:.2e}, errors vs oracle {_err(a[pix], ref):.2e} / {_err(b[pix], ref):.2e}")
+    assert d_ab <= 2e-6
+    assert np.max(np.abs(a[pix] - ref)) / rms <= TOL32 and np.max(np.abs(b[pix] - ref)) / rms <= TOL32
+
+
 def test_map_pixel_list_range_accumulate_ragged(isw):
     w = synth.config(0, seed=2)
     S, _, _ = oracle.lightcone_workload(w)
