@@ -18,7 +18,7 @@
 // records of a tile staged in shared memory by 1-D bulk copies and read by every thread.
 // FP32 kernel: a pixel tile whose bounding cap is at least d_far from the sample tile's cap (and
 // outside its beam cap) is staged as pixel-pair records and summed by a packed f32x2 loop, two
-// pixels per instruction, from the far-field form of the sums (adj_far_stage: 33 FP32 lane
+// pixels per instruction, from the far-field form of the sums (adj_far_stage: 32 FP32 lane
 // operations and two reciprocals per pair); other tiles go through the checked loop (float-pair
 // d, cancellation-free B, FP64 for near pairs).  Per-chunk gradients are reduced over chunks in a
 // fixed order (deterministic).
@@ -177,7 +177,7 @@ __global__ void k_pack_pixels(const double *__restrict__ nv, int64_t ldn, const 
 //   gq = g/Q,  ga = gq A/B,  gT = g N/(BQ),  ge = gT/Q,  w = gq + ga (X'.d)/B,  [u = ga + gq (X'.d)/B]
 // and the partial sums  S2 = sum gq, S3 = sum ga, S4 = sum gT, V1 = sum ge d, V2 = sum w n
 // [V3 = sum u n]; the signs of N, gT, ge are carried negated so that every step is a plain
-// packed multiply or multiply-add: 33 FP32 lane operations and two reciprocals per pair (ngrad 6).
+// packed multiply or multiply-add: 32 FP32 lane operations and two reciprocals per pair (ngrad 6).
 // Per window of 32 pixel pairs the partials are converted into the accumulator layout of the
 // checked loop (adj_pair32): acc0 += (e - 1) S2 - f S3, acc1 += S2, acc2 += S3, acc3 += S4,
 // acc4..6 += 2 V1, acc7..9 += V2 - S2 Xhat, acc10..12 += V3 - S3 Xhat  (|d| >= d_far bounds the
@@ -212,8 +212,9 @@ __device__ __forceinline__ void adj_far_stage(const ulonglong2 *__restrict__ fr,
             const uint64_t iQ = f2_pack(rcp_approx(q0), rcp_approx(q1));
             const uint64_t iB = f2_pack(rcp_approx(b0), rcp_approx(b1));
             const uint64_t gq = f2_mul(g, iQ);
-            const uint64_t ga = f2_mul(gq, f2_mul(A, iB));
-            const uint64_t gTn = f2_mul(Nn, f2_mul(gq, iB));               // -gT
+            const uint64_t gqb = f2_mul(gq, iB);                           // g/(BQ)
+            const uint64_t ga = f2_mul(gqb, A);
+            const uint64_t gTn = f2_mul(gqb, Nn);                          // -gT
             const uint64_t gen = f2_mul(gTn, iQ);                          // -ge
             const uint64_t t1 = f2_mul(Qd, iB);
             const uint64_t w = f2_fma(ga, t1, gq);

@@ -98,3 +98,29 @@ def test_lightcone_adjoint_empty(isw):
     assert gn.shape[1] == 0 and torch.count_nonzero(gl).item() == 0
     r, _ = isw.default_context().check_status()
     assert r == isw.OK
+
+
+@pytest.mark.parametrize("n", [1, 2, 1023, 1024, 1025, 3000])
+def test_map_sample_counts_around_sort_blocks(isw, n):
+    """The FP32 map's spatial sort works on blocks of 1024 samples: counts at and around the block
+    size, and samples that all share one direction (equal sort keys: the stable order decides),
+    against the oracle."""
+    w = synth.config(1, seed=6)
+    S, _, st = oracle.lightcone_workload(w)
+    assert np.all(st == 0)
+    S = np.ascontiguousarray(S[:, 119808:119808 + n])       # random-walk string samples (scattered)
+    nside = 16
+    ref, _ = oracle.isw_map(nside, S, threads=8)
+    got = isw.isw_map(nside, _d(S), prec="f32c").cpu().numpy()
+    r, _ = isw.default_context().check_status()
+    assert r == isw.OK
+    rms = np.sqrt(np.mean(ref ** 2))
+    assert np.max(np.abs(got - ref)) / rms <= 1e-5
+    # the same direction for every sample (one Morton key), different velocities
+    T = S.copy()
+    T[0:3] = S[0:3, :1]
+    ref2, _ = oracle.isw_map(nside, T, threads=8)
+    got2 = isw.isw_map(nside, _d(T), prec="f32c").cpu().numpy()
+    assert isw.default_context().check_status()[0] == isw.OK
+    rms2 = np.sqrt(np.mean(ref2 ** 2))
+    assert np.max(np.abs(got2 - ref2)) / rms2 <= 1e-5
