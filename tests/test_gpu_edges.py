@@ -1,6 +1,8 @@
 """Edge cases of the newer entry points, on the GPU: empty inputs, single-pixel patches, a
 non-orthonormal frame, samples behind the patch plane, l_max = 0, empty boxes, mixed
 LINEAR/BURDEN shells in one solve (bit-exact against the oracle) and an empty adjoint."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -124,3 +126,16 @@ def test_map_sample_counts_around_sort_blocks(isw, n):
     assert isw.default_context().check_status()[0] == isw.OK
     rms2 = np.sqrt(np.mean(ref2 ** 2))
     assert np.max(np.abs(got2 - ref2)) / rms2 <= 1e-5
+
+
+def test_fma_rate_calibration(isw):
+    """isw_fma_rate: the FP32 and FP64 FMA-pipe throughputs the kernels are stated against are
+    positive and ordered as on the hardware (GB300's FP64 unit is a small fraction of FP32)."""
+    ctx = isw.default_context()
+    f32 = ctx.fma_rate("f32c")
+    f64 = ctx.fma_rate("f64")
+    assert f32 > 1e12 and f64 > 1e10
+    assert f32 > 10 * f64
+    v = ctypes.c_double()
+    assert isw.lib().isw_fma_rate(ctx.handle, 7, ctypes.byref(v), None) == isw.EINVAL   # unknown precision
+    assert isw.lib().isw_fma_rate(ctx.handle, isw.F64, None, None) == isw.EINVAL        # no output
