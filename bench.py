@@ -611,7 +611,7 @@ def main():
     ap.add_argument("--split", type=int, default=0, help="segment chunks (0 = automatic)")
     ap.add_argument("--d-far", type=float, default=None, help="far-field chord threshold (library default 0.25)")
     ap.add_argument("--b-min", type=float, default=None, help="FP64 routing threshold on 1 + n.Xdot (default 0.01)")
-    ap.add_argument("--near-k", type=float, default=None, help="near-field radius factor (default 4)")
+    ap.add_argument("--near-k", type=float, default=None, help="near-field radius factor (default 2)")
     ap.add_argument("--nside", type=int, default=None,
                     help="override the sky resolution (smaller skies for profiling; the bench line uses 512)")
     ap.add_argument("--case", choices=["map_f64", "map_f32c", "adjoint_f32c", "adjoint_f64"], default=None,

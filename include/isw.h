@@ -93,7 +93,7 @@ const char *isw_last_error(const isw_ctx *ctx);
  * non-finite weight), pairs that the FP32 path evaluated in FP64 (near field). */
 int isw_check_status(isw_ctx *ctx, void *stream, int64_t *counts);
 
-/* Tunables: ISW_PARAM_NEAR_K (default 4): a pair is "near" when the chord |n - Xhat| is
+/* Tunables: ISW_PARAM_NEAR_K (default 2): a pair is "near" when the chord |n - Xhat| is
  * below near_k * max(pixel size, angular length of the sample's segment); ISW_PARAM_B_MIN
  * (default 0.01): a pair with 1 + n.Xdot below b_min is evaluated in FP64 by the FP32 path;
  * ISW_PARAM_SPLIT: number of segment chunks of the forward maps (0 = automatic);

@@ -328,9 +328,9 @@ int isw_create(isw_ctx **out, int device)
     isw_ctx *c = (isw_ctx *)calloc(1, sizeof(isw_ctx));
     if (!c) return ISW_ENOMEM;
     c->device = device;
-    c->near_k = 4.0;
-    c->b_min = 0.01;
-    c->d_far = 0.25;
+    c->near_k = kNearK;
+    c->b_min = kBMin;
+    c->d_far = kDFar;
     c->split_override = 0;
     c->tile_override = -1;
     c->wait_polls = kWaitPolls;

@@ -449,6 +449,15 @@ struct __align__(16) SegCap {
                 // chord radius enlarged by the B < b_min cone; radius < 0 when there is no such sample
 };
 
+// Default tunables of the FP32 map (isw_map and the allocation-free entry point use the same):
+// near-field radius in units of max(pixel size, segment angle) (2: four pixel radii; 4 measured
+// 318.5 against 312.8 ms per bench step with the same largest error, 7.3e-7 of the rms on the
+// pixels nearest the strings), the 1 + n.Xdot below which a pair goes to FP64, and the tile-cap
+// gap beyond which the far-field form is used.
+constexpr double kNearK = 2.0;
+constexpr double kBMin = 0.01;
+constexpr double kDFar = 0.25;
+
 struct Tunables {
     int threads;    // threads per CTA (FP32 map)
     int ppt;        // pixels per thread

@@ -159,9 +159,9 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     Far2 *far = (Far2 *)(b + off_far);
     const uint32_t *perm = launch_spatial_order(samples, n, ld, xo[0], xo[1], xo[2], b + off_sort, s);
     Mid2 *mid = (Mid2 *)(b + off_mid);
-    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, 4.0, n_pad, perm, s32, s64, far, mid, nullptr, st,
+    launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, kNearK, n_pad, perm, s32, s64, far, mid, nullptr, st,
                 s);
-    launch_seg_caps(s32, s64, n, n_pad, S, 0.01f, scaps, s);
+    launch_seg_caps(s32, s64, n, n_pad, S, (float)kBMin, scaps, s);
     MapArgs a;
     a.nv = nv;
     a.ldn = tot;
@@ -176,8 +176,8 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
     a.scaps = scaps;
     a.nst = nst;
     a.split = split;
-    a.b_min = 0.01f;
-    a.d_far = 0.25f;
+    a.b_min = (float)kBMin;
+    a.d_far = (float)kDFar;
     a.theta = theta_out;
     a.partial = split > 1 ? partial : nullptr;
     a.accumulate = 0;
