@@ -20,8 +20,10 @@
 // outside its beam cap) is staged as pixel-pair records and summed by a packed f32x2 loop, two
 // pixels per instruction, from the far-field form of the sums (adj_far_stage: 32 FP32 lane
 // operations and two reciprocals per pair); other tiles go through the checked loop (float-pair
-// d, cancellation-free B, FP64 for near pairs).  Per-chunk gradients are reduced over chunks in a
-// fixed order (deterministic).
+// d, cancellation-free B, FP64 for near pairs).  FP64 kernel: the same sums in FP64 from Pix64
+// records, far tiles in the far-field form with Newton-refined reciprocals (rcp64), the others
+// pair by pair in the d form with IEEE divisions.  Per-chunk gradients are reduced over chunks in
+// a fixed order (deterministic).
 #include "isw_internal.cuh"
 #include "kernels.cuh"
 #include "pipeline.cuh"
@@ -440,6 +442,10 @@ __global__ void __launch_bounds__(NT) k_adj_f64(AdjArgs a)
         const int nt = (int)(p1 - p0);
         const int64_t s = st * NT + tid;
         const Seg64 s64 = a.s64[s];
+        const SegCap sc = a.scaps[st];
+        const double xh[3] = {s64.xh[0] + s64.xl[0], s64.xh[1] + s64.xl[1], s64.xh[2] + s64.xl[2]};
+        const double e1 = 1.0 + (s64.xd[0] * xh[0] + s64.xd[1] * xh[1] + s64.xd[2] * xh[2]);   // 1 + Xdot.Xhat
+        const double f1 = s64.xp[0] * xh[0] + s64.xp[1] * xh[1] + s64.xp[2] * xh[2];           // X'.Xhat
         double acc[kAcc];
         for (int k = 0; k < kAcc; ++k) acc[k] = 0.0;
         if (tid == 0) {
@@ -456,12 +462,53 @@ __global__ void __launch_bounds__(NT) k_adj_f64(AdjArgs a)
                 const Pix64 *sp = sbuf + buf * TP;
                 double part[kAcc];
                 for (int k = 0; k < kAcc; ++k) part[k] = 0.0;
-                unsigned z = 0;
-                for (int q = 0; q < TP; ++q) {
-                    const Pix64 px = sp[q];
-                    if (px.g != 0.0) adj_pair64(px.n[0], px.n[1], px.n[2], px.g, s64, NG, part, z);
+                // far pixel tile (cap gap >= d_far): the far-field sums of adj_far_stage in FP64
+                const float4 pc = a.pcaps[p0 + i];
+                const float ex = pc.x - sc.c.x, ey = pc.y - sc.c.y, ez = pc.z - sc.c.z;
+                if (sqrtf(ex * ex + ey * ey + ez * ez) - pc.w - sc.c.w >= a.d_far) {
+                    double S2 = 0.0, S3 = 0.0, S4 = 0.0, V1[3] = {0.0, 0.0, 0.0}, V2[3] = {0.0, 0.0, 0.0},
+                           V3[3] = {0.0, 0.0, 0.0};
+                    for (int q = 0; q < TP; ++q) {
+                        const Pix64 px = sp[q];
+                        const double dx = px.n[0] - xh[0], dy = px.n[1] - xh[1], dz = px.n[2] - xh[2];
+                        const double Q = fma(dz, dz, fma(dy, dy, dx * dx));
+                        const double A = fma(px.n[2], s64.xp[2], fma(px.n[1], s64.xp[1], px.n[0] * s64.xp[0]));
+                        const double B = fma(px.n[2], s64.xd[2], fma(px.n[1], s64.xd[1], fma(px.n[0], s64.xd[0], 1.0)));
+                        const double Qd = A - f1;
+                        const double Nn = fma(B, e1 - B, A * Qd);   // -(B Xdot.d - A X'.d)
+                        const double iBQ = rcp64(B * Q), iQ = B * iBQ, iB = Q * iBQ;
+                        const double gq = px.g * iQ, gqb = px.g * iBQ;
+                        const double ga = gqb * A, gTn = gqb * Nn, gen = gTn * iQ;
+                        const double t1 = Qd * iB, w = fma(ga, t1, gq);
+                        S2 += gq;
+                        S3 += ga;
+                        S4 += gTn;
+                        V1[0] = fma(gen, dx, V1[0]);
+                        V1[1] = fma(gen, dy, V1[1]);
+                        V1[2] = fma(gen, dz, V1[2]);
+                        for (int c = 0; c < 3; ++c) V2[c] = fma(w, px.n[c], V2[c]);
+                        if (NG >= 9) {
+                            const double u = fma(gq, t1, ga);
+                            for (int c = 0; c < 3; ++c) V3[c] = fma(u, px.n[c], V3[c]);
+                        }
+                    }
+                    part[0] = (e1 - 1.0) * S2 - f1 * S3;
+                    part[1] = S2;
+                    part[2] = S3;
+                    part[3] = -S4;
+                    for (int c = 0; c < 3; ++c) {
+                        part[4 + c] = -2.0 * V1[c];
+                        part[7 + c] = V2[c] - S2 * xh[c];
+                        part[10 + c] = V3[c] - S3 * xh[c];
+                    }
+                } else {
+                    unsigned z = 0;
+                    for (int q = 0; q < TP; ++q) {
+                        const Pix64 px = sp[q];
+                        if (px.g != 0.0) adj_pair64(px.n[0], px.n[1], px.n[2], px.g, s64, NG, part, z);
+                    }
+                    if (s < a.n) zerocnt += z;
                 }
-                if (s < a.n) zerocnt += z;
                 for (int k = 0; k < kAcc; ++k) acc[k] += part[k];
             }
             __syncthreads();

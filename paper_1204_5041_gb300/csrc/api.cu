@@ -908,10 +908,8 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     launch_pack(samples, n, ld, xo[0], xo[1], xo[2], GU, theta_pix, c->near_k, n_pad, nullptr, s32, s64, nullptr,
                 nullptr, nullptr, c->d_status, s);
     c->n_launch += 4;
-    if (prec == ISW_F32C) {
-        launch_seg_caps(s32, s64, n, n_pad, NT, (float)c->b_min, scaps, s);
-        c->n_launch += 1;
-    }
+    launch_seg_caps(s32, s64, n, n_pad, NT, (float)c->b_min, scaps, s);
+    c->n_launch += 1;
     AdjArgs a;
     a.p32 = p32;
     a.p64 = p64;

@@ -505,18 +505,6 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
     }
 }
 
-// 1/x for a positive normal double within the float range: the FP32 hardware estimate refined by
-// two Newton steps (relative error ~2^-22 -> 2^-44 -> below an ulp), five FP64 operations
-// instead of the IEEE division's longer sequence.
-__device__ __forceinline__ double rcp64(double x)
-{
-    double r = (double)rcp_approx((float)x);
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
-}
-
 // Plain FP64 path: every pair in FP64, same tiling.  Segment tiles whose cap is at least d_far
 // from the pixel tile's cap are evaluated in the FP64 far-field form
 // t = (c/2) [B (B - e) - A (A - f)] / [B (1 - n.Xhat)] (Far64 records: the cancellation in
