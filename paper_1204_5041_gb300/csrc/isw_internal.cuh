@@ -421,12 +421,15 @@ __device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
 struct __align__(16) Seg64 {
     double xh[3], xl[3], xd[3], xp[3], c, om, X, cu;   // X = |X_s - x_obs|
 };
-// Far-field constants of one sample for the FP64 kernel: -Xhat (3), Xdot (3), X' (3), c/2,
-// e = 1 + Xdot.Xhat, f = X'.Xhat, so that for |d| >= d_far the pair term is
-// t = (c/2) [B (B - e) - A (A - f)] / [B (1 - n.Xhat)]  (d.d = 2 (1 - n.Xhat), Xdot.d = B - e,
-// X'.d = A - f).
+// Far-field constants of one sample for the FP64 kernel, the completed-square form of the FP32
+// far pass in FP64 (sigma = sign(c), s = sqrt(|c|/2), e = 1 + Xdot.Xhat, f = X'.Xhat):
+// mxh = -sigma Xhat, sg = sigma, xd = Xdot, sx = s, be = -s e/2, xp = s X', af = -s f/2,
+// K = (|c|/2) (e^2 - f^2)/4, so that for |d| >= d_far the pair term is
+// t = [(s B - s e/2)^2 - (s A - s f/2)^2 - K] / [B sigma (1 - n.Xhat)]
+//   = (c/2) [B (B - e) - A (A - f)] / [B (1 - n.Xhat)]  (d.d = 2 (1 - n.Xhat), Xdot.d = B - e,
+// X'.d = A - f).  A zero-weight sample has s = 0 and K = 0: its terms are exactly zero.
 struct __align__(16) Far64 {
-    double mxh[3], xd[3], xp[3], ch, e, f;
+    double mxh[3], sg, xd[3], sx, be, xp[3], af, K;
 };
 // Pixel records of the adjoint: FP32 (n hi, g | n lo, 0) and FP64 (n, g); padding slots
 // hold n = 0, g = 0 so that every pair stays finite and contributes nothing.

@@ -507,9 +507,10 @@ __global__ void __launch_bounds__(NT, (P <= 4 ? 512 : 256) / NT) k_map_f32c_near
 
 // Plain FP64 path: every pair in FP64, same tiling.  Segment tiles whose cap is at least d_far
 // from the pixel tile's cap are evaluated in the FP64 far-field form
-// t = (c/2) [B (B - e) - A (A - f)] / [B (1 - n.Xhat)] (Far64 records: the cancellation in
-// 1 - n.Xhat costs at most a factor 2/d_far^2 = 32 of the 1e-16 rounding); the others pair by
-// pair from d = n - Xhat formed from the double-double Xhat, with the IEEE division.
+// t = (c/2) [B (B - e) - A (A - f)] / [B (1 - n.Xhat)], written with completed squares scaled by
+// sqrt(|c|/2) (Far64 records: 17 FP64 operations per pair; the cancellation in 1 - n.Xhat costs
+// at most a factor 2/d_far^2 = 32 of the 1e-16 rounding); the others pair by pair from
+// d = n - Xhat formed from the double-double Xhat, with the IEEE division.
 template <int NT, int P, int S>
 __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
 {
@@ -586,11 +587,12 @@ __global__ void __launch_bounds__(NT) k_map_f64(MapArgs a)
                         const Far64 r = fb[s];
 #pragma unroll
                         for (int q = 0; q < P; ++q) {
-                            const double h1 = fma(nv[q][2], r.mxh[2], fma(nv[q][1], r.mxh[1], fma(nv[q][0], r.mxh[0], 1.0)));
+                            const double hs = fma(nv[q][2], r.mxh[2], fma(nv[q][1], r.mxh[1], fma(nv[q][0], r.mxh[0], r.sg)));
                             const double B = fma(nv[q][2], r.xd[2], fma(nv[q][1], r.xd[1], fma(nv[q][0], r.xd[0], 1.0)));
-                            const double A = fma(nv[q][2], r.xp[2], fma(nv[q][1], r.xp[1], nv[q][0] * r.xp[0]));
-                            const double num = fma(B, B - r.e, -(A * (A - r.f)));
-                            part[q] = fma(r.ch * num, rcp64(B * h1), part[q]);
+                            const double A2 = fma(nv[q][2], r.xp[2], fma(nv[q][1], r.xp[1], fma(nv[q][0], r.xp[0], r.af)));
+                            const double B2 = fma(r.sx, B, r.be);
+                            const double num = fma(-A2, A2, fma(B2, B2, -r.K));
+                            part[q] = fma(num, rcp64(B * hs), part[q]);
                         }
                     }
                 } else {

@@ -153,14 +153,20 @@ __global__ void k_pack(const double *__restrict__ S, int64_t n, int64_t ld, doub
         if (far64) {
             Far64 r;
             const double xh[3] = {g.xh[0] + g.xl[0], g.xh[1] + g.xl[1], g.xh[2] + g.xl[2]};
+            const double ch = 0.5 * g.c;
+            const double sg = ch < 0.0 ? -1.0 : 1.0, sq = sqrt(fabs(ch));
+            const double e1 = 1.0 + (g.xd[0] * xh[0] + g.xd[1] * xh[1] + g.xd[2] * xh[2]);
+            const double f1 = g.xp[0] * xh[0] + g.xp[1] * xh[1] + g.xp[2] * xh[2];
             for (int k = 0; k < 3; ++k) {
-                r.mxh[k] = -xh[k];
+                r.mxh[k] = -sg * xh[k];
                 r.xd[k] = g.xd[k];
-                r.xp[k] = g.xp[k];
+                r.xp[k] = sq * g.xp[k];
             }
-            r.ch = 0.5 * g.c;
-            r.e = 1.0 + (g.xd[0] * xh[0] + g.xd[1] * xh[1] + g.xd[2] * xh[2]);
-            r.f = g.xp[0] * xh[0] + g.xp[1] * xh[1] + g.xp[2] * xh[2];
+            r.sg = sg;
+            r.sx = sq;
+            r.be = -0.5 * sq * e1;
+            r.af = -0.5 * sq * f1;
+            r.K = fabs(ch) * 0.25 * (e1 * e1 - f1 * f1);
             far64[s] = r;
         }
         if (far) {

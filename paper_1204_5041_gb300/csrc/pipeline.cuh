@@ -26,7 +26,7 @@ __device__ __forceinline__ double pair64(double nx, double ny, double nz, const 
     return g.c * (B * Pd - A * Qd) / (B * Q);
 }
 
-// 1/x for a positive normal double within the float range: the FP32 hardware estimate r
+// 1/x for a nonzero normal double of either sign within the float range: the FP32 estimate r
 // (relative error e = 1 - x r below ~2^-22) refined by one third-order step of the iteration for
 // 1/x, r (1 + e + e^2) (error e^3 < 2^-66, below an ulp): three FP64 FMAs and two conversions
 // instead of the IEEE division's longer sequence.
