@@ -89,6 +89,24 @@ def test_adjoint_vs_oracle_small(isw, small, prec, tol):
         assert e <= tol
 
 
+def test_adjoint_mixed_sign_weights(isw, small):
+    """dsigma of random sign (weights of both signs in every tile) and a negative GU, against the
+    oracle's gradient; the gradient is linear in GU at fixed g."""
+    N, S, th, target, g, _ = small
+    S2 = S.copy()
+    flip = np.random.default_rng(22).random(S.shape[1]) < 0.5
+    S2[9, flip] *= -1.0
+    ref = oracle.isw_map_adjoint(N, S2, g, ngrad=10, threads=THREADS)
+    for prec, tol in (("f64", 1e-10), ("f32c", 1e-6)):
+        got = isw.isw_map_adjoint(N, _d(S2), _d(g), prec=prec, ngrad=10).cpu().numpy()
+        assert isw.default_context().check_status()[0] == isw.OK
+        neg = isw.isw_map_adjoint(N, _d(S2), _d(g), prec=prec, ngrad=10, GU=-1.0).cpu().numpy()
+        e, en = _blockerr(got[:9], ref[:9]), _blockerr(neg[:9], -ref[:9])
+        e10 = np.max(np.abs(got[9] - ref[9])) / np.max(np.abs(ref[9]))
+        print(f"adjoint mixed-sign {prec}: {e:.3e}, at -GU {en:.3e}, dsigma row {e10:.3e}")
+        assert e <= tol and en <= tol and e10 <= tol
+
+
 def test_adjoint_splits_and_list(isw, small):
     N, S, th, target, g, ref = small
     ctx = isw.default_context()

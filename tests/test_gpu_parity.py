@@ -165,6 +165,26 @@ def test_map_deterministic(isw, cfg0):
         assert np.array_equal(a.view(np.int64), b.view(np.int64))
 
 
+def test_map_mixed_sign_weights(isw, cfg0):
+    """Weights c = -4 GU eps dsigma / X of both signs in every tile (dsigma of random sign) and a
+    negative GU: the far-field forms carry sign(c) and sqrt(|c|/2) separately, so both signs must
+    reach the oracle's map, and by the linearity of Eq. (1) in GU the map at -GU is the negated
+    map."""
+    w, S, _ = cfg0
+    S2 = S.copy()
+    flip = np.random.default_rng(21).random(S.shape[1]) < 0.5
+    S2[9, flip] *= -1.0
+    ref, _ = oracle.isw_map(w.nside, S2, threads=THREADS)
+    Sd = _d(S2)
+    for prec, tol in (("f64", TOL64), ("f32c", TOL32)):
+        got = isw.isw_map(w.nside, Sd, prec=prec).cpu().numpy()
+        assert _status_ok(isw)[0] == isw.OK
+        neg = isw.isw_map(w.nside, Sd, prec=prec, GU=-1.0).cpu().numpy()
+        e, en = _err(got, ref), _err(neg, -ref)
+        print(f"mixed-sign weights {prec}: max|d|/rms = {e:.3e}, at -GU {en:.3e}")
+        assert e <= tol and en <= tol
+
+
 def test_map_independent_of_sample_order(isw):
     """The FP32 path writes its records in a spatial (Morton) order of the samples: a permuted
     input gives the same map up to the rounding of the different summation order, and both match
