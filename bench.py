@@ -139,7 +139,7 @@ def kernel_sources_sha1() -> str:
     import hashlib
 
     h = hashlib.sha1()
-    for f in ("map.cu", "pipeline.cuh", "isw_internal.cuh", "pack.cu"):
+    for f in ("map.cu", "pipeline.cuh", "isw_internal.cuh", "pack.cu", "api.cu", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_1204_5041_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

@@ -137,7 +137,7 @@ extern "C" int isw_map_f32c_noalloc(int64_t nside, int64_t pix0, int64_t npix, c
 
     // segment chunks: the rule isw_map uses, capped by the scratch left
     const int slots = map_f32c_slots(0, sms);
-    const int split = choose_split(ntiles, nst, slots, (int)(room < 64 ? room : 64));
+    const int split = choose_split(ntiles, nst, slots, (int)(room < 64 ? room : 64), kMapItemsPerSlot);
     unsigned char *b = (unsigned char *)base;
     DevStatus *st = (DevStatus *)(b + off[0]);
     double *nv = (double *)(b + off[1]);
