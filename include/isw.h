@@ -96,7 +96,10 @@ int isw_check_status(isw_ctx *ctx, void *stream, int64_t *counts);
 /* Tunables: ISW_PARAM_NEAR_K (default 2): a pair is "near" when the chord |n - Xhat| is
  * below near_k * max(pixel size, angular length of the sample's segment); ISW_PARAM_B_MIN
  * (default 0.01): a pair with 1 + n.Xdot below b_min is evaluated in FP64 by the FP32 path;
- * ISW_PARAM_SPLIT: number of segment chunks of the forward maps (0 = automatic);
+ * ISW_PARAM_SPLIT: number of segment chunks of the forward maps (0 = automatic: enough
+ * (pixel tile, chunk) work items to fill every resident CTA in near-equal waves and at least 64
+ * per resident CTA, while each chunk keeps 256 segment tiles; chunk partials cost 8 bytes per
+ * pixel and chunk of device memory);
  * ISW_PARAM_VARIANT: FP32 kernel variant (-1 = automatic); ISW_PARAM_D_FAR (default 0.25):
  * segment tiles whose every pair is at least this chord apart from the pixel tile use the
  * FP32 far-field form (d.d = 2 (1 - n.Xhat), Xdot.d and X'.d from per-sample constants);
