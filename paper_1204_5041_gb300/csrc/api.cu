@@ -145,10 +145,10 @@ PixelPlan plan_pixels(int64_t N, int64_t pix0, int64_t npix, const int64_t *pix_
 // Number of segment chunks: enough work items to fill every resident CTA slot with
 // near-equal waves, at least two segment tiles per chunk, at most max_split chunks.  With
 // min_items > 0 the count then grows while there are fewer than min_items work items per slot
-// and every chunk keeps at least 256 segment tiles: items are taken from a global counter, so the
-// last ones leave slots idle for about half an item's time, and shorter items shorten that tail
-// (N_side 512 with 2e5 samples: 314 ms per map with 4 chunks, 310 ms with 8-12).
-int isw::choose_split(int64_t ntiles, int64_t nst, int slots, int max_split, int min_items)
+// and every chunk keeps at least min_chunk streamed tiles: items are taken from a global counter,
+// so the last ones leave slots idle for about half an item's time, and shorter items shorten that
+// tail (N_side 512 with 2e5 samples: 314 ms per map with 4 chunks, 310 ms with 8-12).
+int isw::choose_split(int64_t ntiles, int64_t nst, int slots, int max_split, int min_items, int min_chunk)
 {
     const double ideal = (double)ntiles / slots;
     int best = 1;
@@ -164,7 +164,7 @@ int isw::choose_split(int64_t ntiles, int64_t nst, int slots, int max_split, int
         }
         if (t <= ideal * 1.01) break;
     }
-    while (best < max_split && ntiles * best < (int64_t)min_items * slots && nst / (best + 1) >= 256) ++best;
+    while (best < max_split && ntiles * best < (int64_t)min_items * slots && nst / (best + 1) >= min_chunk) ++best;
     return best;
 }
 
@@ -884,7 +884,8 @@ int isw_map_adjoint(isw_ctx *c, int64_t nside, int64_t pix0, int64_t npix, const
     const int64_t n_pad = (n + NT - 1) / NT * NT;
     const int64_t nseg_tiles = n_pad / NT;
     const int slots = adj_slots(prec, ngrad, c->num_sms);
-    int split = c->split_override > 0 ? c->split_override : choose_split(nseg_tiles, pp.ntiles, slots, 64);
+    int split = c->split_override > 0 ? c->split_override
+                                      : choose_split(nseg_tiles, pp.ntiles, slots, 64, kAdjItemsPerSlot, kAdjMinChunk);
     if (split > pp.ntiles) split = (int)pp.ntiles;
     if ((r = ensure_ws(c, kWsNv, (size_t)pp.tot * 3 * sizeof(double)))) return r;
     if ((r = ensure_ws(c, kWsOut, (size_t)pp.tot * sizeof(int64_t)))) return r;

@@ -8,8 +8,10 @@ namespace isw {
 // api.cu: number of work chunks along the streamed axis for ntiles tiles of the other axis, nst
 // streamed tiles and `slots` resident CTAs (near-equal waves; at least two streamed tiles per
 // chunk; at most max_split chunks)
-int choose_split(int64_t ntiles, int64_t nst, int slots, int max_split, int min_items = 0);
+int choose_split(int64_t ntiles, int64_t nst, int slots, int max_split, int min_items = 0, int min_chunk = 256);
 constexpr int kMapItemsPerSlot = 64;   // work items per CTA slot that the map's chunk count aims at
+constexpr int kAdjItemsPerSlot = 64;   // the same for the adjoint's pixel chunks,
+constexpr int kAdjMinChunk = 32;       // each chunk keeping at least this many pixel tiles
 
 // probe.cu: FMA-pipe throughput (flop/s, FMA = 2) of the FP32 or FP64 pipe; sink is never written
 int fma_probe(bool f64, int num_sms, double *sink, double *flops, cudaStream_t s);
